@@ -1,0 +1,44 @@
+"""Write tests/golden/fstar.json: optimal objective values of the measured configurations.
+
+Every number here comes from the FP64 oracle (oracle/) run on the seeded
+inputs of workloads/ to its precision floor (Frank-Wolfe certificate 1e-13 or
+no decrease of f for 30 iterations).  Nothing here touches the CUDA path.
+
+    python tests/golden/make_golden.py [c0 c1 c2 ...]
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+import workloads as W  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fstar.json")
+CONFIGS = {"c0": W.config0, "c1": W.config1, "c2": W.config2}
+
+
+def main(names):
+    gold = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for name in names:
+        t = time.time()
+        prob = CONFIGS[name]()
+        x, res, _ = oracle.reference_solve(prob)
+        gold[name] = {
+            "workload": prob.name, "n": prob.n, "p": prob.p, "rho": prob.rho,
+            "f_star": res.f, "lambda": res.lambda_reg, "l1": res.l1, "fw_gap": res.fw_gap,
+            "x_norm2": float(np.linalg.norm(x)), "nnz": int(np.count_nonzero(x)),
+            "iters": res.iters, "stop": oracle.STOP_NAMES[res.stop],
+        }
+        print(name, gold[name], f"{time.time() - t:.1f}s", flush=True)
+        with open(OUT, "w") as fh:
+            json.dump(gold, fh, indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or list(CONFIGS))

@@ -1,0 +1,313 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each check below would fail for a plausible slip in the oracle: a dropped
+factor 2 in the gradient, a swapped BB rule, a wrong direction of the ratio
+test or of the tau update, an off-by-one in the sorted projection, a sign
+error in the soft threshold, an Armijo test with the wrong sign.
+
+* Projection onto the l1 ball (the paper uses P_Omega without giving an
+  algorithm): brute force over supports and signs, identity inside the ball,
+  l1 norm equal to rho on the boundary, soft-threshold form with a threshold
+  found by bisection, the variational inequality of a Euclidean projection.
+* Algorithm GP + SS on eq. 2:
+    - the closed form for K with orthonormal columns (the solution is the
+      projection of K^T y), reached by the first BB step, which equals 1/2;
+    - brute force over supports and signs for tiny p (n >= p);
+    - the equivalence of eq. 1 and eq. 2 and the lambda-rho relation of Sec. 1,
+      checked with FISTA (eq. fista), an independent algorithm for eq. 1;
+    - the KKT sign conditions on the configurations;
+    - a 3-iteration trace on a diagonal problem derived by hand (below);
+    - monotone decrease (M = 1), feasibility, steplength bounds.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+
+def brute_project(v, rho):
+    """min ||w - v||^2 over ||w||_1 <= rho by enumerating sign patterns sigma in {-1,0,1}^p.
+
+    For a fixed sign pattern with support S the minimiser on the face
+    sigma^T w_S = rho is w_S = v_S - ((sigma^T v_S - rho)/|S|) sigma; it is a
+    candidate when its signs agree with sigma.
+    """
+    v = np.asarray(v, float)
+    if np.abs(v).sum() <= rho:
+        return v.copy()
+    best, best_w = np.inf, None
+    for sig in itertools.product((-1, 0, 1), repeat=v.size):
+        sig = np.array(sig, float)
+        S = sig != 0
+        if not S.any():
+            continue
+        w = np.zeros_like(v)
+        w[S] = v[S] - (sig[S] @ v[S] - rho) / S.sum() * sig[S]
+        if np.any(sig[S] * w[S] < -1e-12):
+            continue
+        dist = ((w - v) ** 2).sum()
+        if dist < best:
+            best, best_w = dist, w
+    return best_w
+
+
+def soft_threshold_bisect(v, rho):
+    """tau with sum(max(|v|-tau, 0)) = rho found by plain bisection."""
+    a = np.abs(v)
+    lo, hi = 0.0, a.max()
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.maximum(a - mid, 0).sum() > rho:
+            lo = mid
+        else:
+            hi = mid
+    tau = 0.5 * (lo + hi)
+    return np.sign(v) * np.maximum(a - tau, 0), tau
+
+
+def brute_eq2(K, y, rho):
+    """min ||Kx - y||^2 s.t. ||x||_1 <= rho by enumerating supports and signs (n >= p).
+
+    Candidates: for every support S the unconstrained least-squares solution
+    (kept if ||x||_1 <= rho) and, for every sign vector sigma on S, the
+    least-squares solution on the face sigma^T x_S = rho (kept if its signs
+    agree with sigma).  The optimum is one of the candidates.
+    """
+    n, p = K.shape
+    best, best_x = np.sum(y ** 2), np.zeros(p)
+    for sig in itertools.product((-1, 0, 1), repeat=p):
+        sig = np.array(sig, float)
+        S = np.flatnonzero(sig)
+        if S.size == 0:
+            continue
+        KS = K[:, S]
+        A = KS.T @ KS
+        b = KS.T @ y
+        # face: [2A  s; s^T 0] [x; mu] = [2b; rho]
+        M = np.zeros((S.size + 1, S.size + 1))
+        M[:-1, :-1] = 2 * A
+        M[:-1, -1] = sig[S]
+        M[-1, :-1] = sig[S]
+        rhs = np.concatenate([2 * b, [rho]])
+        sol = np.linalg.solve(M, rhs)
+        xs = sol[:-1]
+        cands = []
+        if np.all(sig[S] * xs >= -1e-12):
+            cands.append(xs)
+        xu = np.linalg.solve(A, b)
+        if np.abs(xu).sum() <= rho:
+            cands.append(xu)
+        for c in cands:
+            x = np.zeros(p)
+            x[S] = c
+            f = np.sum((K @ x - y) ** 2)
+            if f < best:
+                best, best_x = f, x
+    return best_x, best
+
+
+def fista(K, y, lam, iters):
+    """FISTA (eq. fista) for min ||Kx - y||^2 + 2 lam ||x||_1, step 1/||K||^2.
+
+    With ||K|| = 1 this is exactly the paper's iteration x <- T(x + ...) with
+    T(x) = S_lam[x + K^T (y - K x)]; here K is rescaled through the step.
+    """
+    L = np.linalg.norm(K, 2) ** 2
+    x = np.zeros(K.shape[1])
+    x_prev = x.copy()
+    t = 1.0
+    for _ in range(iters):
+        t_next = (1 + np.sqrt(1 + 4 * t * t)) / 2
+        u = x + (t - 1) / t_next * (x - x_prev)
+        w = u + K.T @ (y - K @ u) / L
+        x_prev = x
+        x = np.sign(w) * np.maximum(np.abs(w) - lam / L, 0)
+        t = t_next
+    return x
+
+
+def dense_problem(K, y, rho):
+    K = np.asarray(K, float)
+    return W.Problem(np.ascontiguousarray(K), K.shape[0], K.shape[1], K.shape[1], W.DT_F64,
+                     np.asarray(y, float), float(rho), np.zeros(K.shape[1]), "dense")
+
+
+# --------------------------------------------------------------- projection
+
+def test_project_identity_inside_ball():
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal(257)
+    w, tau = oracle.project(v, np.abs(v).sum() * 1.0001)
+    assert tau == 0.0
+    assert np.array_equal(w, v)
+    w, tau = oracle.project(v, np.abs(v).sum())          # exactly on the boundary
+    assert np.array_equal(w, v)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_project_brute_force_tiny(seed):
+    rng = np.random.default_rng(100 + seed)
+    p = int(rng.integers(1, 8))
+    v = rng.standard_normal(p) * rng.choice([0.1, 1, 10])
+    if seed % 3 == 0:
+        v[rng.integers(0, p)] = 0.0                      # sgn(0) = 0
+    if seed % 4 == 1 and p > 1:
+        v[1] = -v[0]                                     # tie in |v|
+    rho = float(rng.uniform(0.05, 1.2) * np.abs(v).sum())
+    w, _ = oracle.project(v, rho)
+    np.testing.assert_allclose(w, brute_project(v, rho), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("p,scale", [(1000, 0.3), (4096, 0.01), (333, 0.9)])
+def test_project_boundary_soft_threshold(p, scale):
+    rng = np.random.default_rng(p)
+    v = rng.standard_normal(p) * np.exp(rng.standard_normal(p))
+    rho = scale * np.abs(v).sum()
+    w, tau = oracle.project(v, rho)
+    assert tau > 0
+    assert abs(np.abs(w).sum() - rho) <= 1e-12 * rho
+    assert np.all(w * v >= 0) and np.all(np.abs(w) <= np.abs(v))
+    wb, taub = soft_threshold_bisect(v, rho)
+    assert abs(tau - taub) <= 1e-12 * max(1.0, taub)
+    np.testing.assert_allclose(w, wb, rtol=0, atol=1e-11 * np.abs(v).max())
+
+
+def test_project_variational_inequality():
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal(64) * 3
+    rho = 5.0
+    w, _ = oracle.project(v, rho)
+    for _ in range(200):
+        u = rng.standard_normal(64)
+        u *= rng.uniform(0, 1) * rho / np.abs(u).sum()   # a point of the ball
+        assert (v - w) @ (u - w) <= 1e-10
+
+
+# --------------------------------------------------------------- GP + SS
+
+def test_hand_derived_trace_diagonal():
+    """K = diag(1, 3), y = (9, 1), rho = 100 (constraint inactive), x0 = 0.
+
+    f(x) = (x1 - 9)^2 + (3 x2 - 1)^2,  grad f = (2 x1 - 18, 18 x2 - 6).
+    k=0: g0 = (-18,-6); P(x0 - g0) = (18, 6) so alpha_0 = 1/18; h = (1, 1/3);
+         f(h) = 64 <= 82 - 2e-3, lambda = 1; x1 = (1, 1/3).
+    k=1: g1 = (-16, 0); s = (1, 1/3), z = (2, 6): s's = 10/9, s'z = 4, z'z = 40;
+         BB1 = 5/18, BB2 = 1/10, ratio 0.36 <= tau_1 = 0.5 -> alpha_1 = min{a2_1}
+         = 1/10 and tau_2 = 0.45; h = (2.6, 1/3), f = 40.96, lambda = 1.
+    k=2: g2 = (-12.8, 0); s = (1.6, 0), z = (3.2, 0): BB1 = BB2 = 1/2, ratio 1 >
+         0.45 -> alpha_2 = 1/2, tau_3 = 0.495; h = (9, 1/3) is the minimiser.
+    """
+    prob = dense_problem(np.diag([1.0, 3.0]), [9.0, 1.0], 100.0)
+    x, res, tr = oracle.gpss(prob, trace=True, tol=0.0, max_iter=10)
+    expect = np.array([[82.0, 1 / 18, 1.0, 0.5],
+                       [64.0, 0.1, 1.0, 0.45],
+                       [40.96, 0.5, 1.0, 0.495]])
+    np.testing.assert_allclose(tr[:3], expect, rtol=1e-12)
+    np.testing.assert_allclose(x, [9.0, 1 / 3], rtol=1e-12)
+
+
+def test_orthonormal_closed_form():
+    """K^T K = I: f(x) = ||x - K^T y||^2 + const, so x* = P(K^T y) = S_tau(K^T y).
+
+    From x0 = 0 the BB steps at k = 1 are both 1/2 (s^T z = 2 s^T s), which
+    sends x_1 - alpha_1 g_1 to K^T y exactly, so x_2 = P(K^T y).  (Further
+    iterations only move x by rounding noise.)
+    """
+    prob = W.orthonormal(300, 120, 15, seed=3, rho_scale=0.5)
+    K = prob.K_f64()
+    xs, tau = soft_threshold_bisect(K.T @ prob.y, prob.rho)
+    x, res, tr = oracle.gpss(prob, trace=True, tol=0.0, max_iter=2)
+    np.testing.assert_allclose(x, xs, atol=1e-12 * np.abs(xs).max())
+    assert abs(tr[1, 1] - 0.5) < 1e-12 and tr[1, 2] == 1.0
+    f, lam, fw, g = oracle.certificates(prob, x)
+    assert abs(lam - tau) <= 1e-9 * tau          # lambda = max|K^T(y - Kx)| = tau here
+    assert abs(f - np.sum((K @ xs - prob.y) ** 2)) <= 1e-10 * f
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_gpss_brute_force_tiny(seed):
+    rng = np.random.default_rng(500 + seed)
+    p = int(rng.integers(2, 7))
+    n = p + int(rng.integers(0, 4))
+    K = rng.standard_normal((n, p))
+    y = rng.standard_normal(n)
+    x_ls = np.linalg.lstsq(K, y, rcond=None)[0]
+    rho = float(rng.uniform(0.1, 1.3) * np.abs(x_ls).sum())
+    xb, fb = brute_eq2(K, y, rho)
+    x, res, _ = oracle.reference_solve(dense_problem(K, y, rho))
+    assert res.f <= fb * (1 + 1e-12) + 1e-14
+    np.testing.assert_allclose(x, xb, atol=1e-7 * max(1, np.abs(xb).max()))
+
+
+def test_lambda_rho_relation_fista():
+    """Eq. 1 at lambda and eq. 2 at rho = ||xbar(lambda)||_1 have the same minimiser,
+    and lambda = max|K^T(y - K x~(rho))| (Sec. 1)."""
+    rng = np.random.default_rng(11)
+    n, p = 60, 150
+    K = rng.standard_normal((n, p)) / np.sqrt(n)
+    x0 = np.zeros(p)
+    x0[rng.permutation(p)[:8]] = rng.standard_normal(8)
+    y = K @ x0 + 0.01 * rng.standard_normal(n)
+    lam_max = np.abs(K.T @ y).max()
+    lam = lam_max / 6
+    xbar = fista(K, y, lam, 30000)
+    rho = np.abs(xbar).sum()
+    x, res, _ = oracle.reference_solve(dense_problem(K, y, rho))
+    np.testing.assert_allclose(x, xbar, atol=1e-7)
+    assert abs(res.lambda_reg - lam) <= 1e-6 * lam
+
+
+def test_lambda_max_zero_solution():
+    """xbar(lambda) = 0 for lambda >= lambda_max = max|K^T y| (Sec. 1)."""
+    rng = np.random.default_rng(12)
+    K = rng.standard_normal((30, 50)) / np.sqrt(30)
+    y = rng.standard_normal(30)
+    lam_max = np.abs(K.T @ y).max()
+    assert np.all(fista(K, y, lam_max * 1.0001, 500) == 0)
+    # on the eq. 2 side: rho -> 0 gives lambda -> lambda_max
+    x, res, _ = oracle.reference_solve(dense_problem(K, y, 1e-9))
+    assert abs(res.lambda_reg - lam_max) <= 1e-6 * lam_max
+
+
+def kkt_check(prob, x, rel=1e-6):
+    f, lam, fw, g = oracle.certificates(prob, x)
+    c = -0.5 * g                                  # c = K^T (y - K x)
+    supp = np.abs(x) > 1e-9 * np.abs(x).max()
+    assert abs(np.abs(x).sum() - prob.rho) <= 1e-9 * prob.rho       # constraint active
+    assert np.all(np.abs(c[supp] - lam * np.sign(x[supp])) <= rel * lam)
+    assert np.all(np.abs(c) <= lam * (1 + 1e-12))
+    return f, lam
+
+
+def test_config0_kkt_and_invariants():
+    prob = W.config0()
+    x, res, _ = oracle.reference_solve(prob)
+    kkt_check(prob, x)
+    # invariants of a 1e-6 run: monotone f (M = 1), feasibility, alpha in range,
+    # tau changed only by 0.9 or 1.1, lambda a power of theta
+    x6, r6, tr = oracle.gpss(prob, trace=True, f_star=res.f, tol=1e-6)
+    assert r6.stop == 0 and (r6.f - res.f) <= 1e-6 * res.f
+    assert np.all(np.diff(tr[:, 0]) <= 0)
+    assert np.all((tr[:, 1] >= 1e-10) & (tr[:, 1] <= 1e10))
+    ratios = tr[1:, 3] / tr[:-1, 3]
+    assert np.all(np.isclose(ratios, 0.9) | np.isclose(ratios, 1.1) | np.isclose(ratios, 1.0))
+    assert np.all(np.isclose(np.log2(tr[:, 2]), np.round(np.log2(tr[:, 2]))))
+    assert np.abs(x6).sum() <= prob.rho * (1 + 1e-12)
+
+
+def test_golden_fstar_values_match_oracle_small():
+    """The stored f* of config 0 was written by tests/golden/make_golden.py from the oracle."""
+    with open(os.path.join(GOLDEN, "fstar.json")) as fh:
+        gold = json.load(fh)
+    prob = W.config0()
+    x, res, _ = oracle.reference_solve(prob)
+    assert abs(res.f - gold["c0"]["f_star"]) <= 1e-12 * res.f
