@@ -1,0 +1,177 @@
+/*
+ * gpl1 -- gradient projection onto the l1 ball with adaptive Barzilai-Borwein
+ * steplengths (GPSS), single GB300 GPU, C ABI.
+ *
+ * Problem (eq. 2, Sec. 1):   minimise f(x) = ||K x - y||^2   subject to ||x||_1 <= rho,
+ * with K an n x p matrix.  The method is Algorithm GP (gradient projection with
+ * a non-monotone Armijo line search along the feasible direction) with
+ * Algorithm SS (adaptive alternation of the two Barzilai-Borwein rules of
+ * eq. (bbrules)), both in Sec. 3; the default parameters are the ones listed at
+ * the end of Sec. 3.
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments are DEVICE pointers owned by the caller, unless a
+ *     comment says otherwise.  The library never frees caller memory.
+ *   - K is row-major: element (i, j) is at K[i * ldk + j], 0 <= i < n,
+ *     0 <= j < p, ldk >= p.  The K pointer must be 16-byte aligned and
+ *     ldk * sizeof(element) must be a multiple of 16 bytes (rows start on
+ *     16-byte boundaries); columns p..ldk-1 are never read.
+ *   - Element types: GPL1_F64 -> K, y, x are double.  GPL1_F32 -> K, y, x are
+ *     float.  GPL1_BF16 -> K is bfloat16 (raw 16-bit patterns), y and x are
+ *     float.  Products with K accumulate in float (double for GPL1_F64); the
+ *     line-search test, the steplength rule and the projection threshold are
+ *     decided in double precision.
+ *   - Work is enqueued on the context's stream (gpl1_create / gpl1_set_stream)
+ *     in stream order.  Calls that return results in host memory synchronise
+ *     that stream before returning.
+ *   - Every function returns a gpl1_status; nothing throws or aborts across
+ *     the ABI.  On GPL1_ERR_INVALID_ARG / GPL1_ERR_UNSUPPORTED nothing was
+ *     enqueued.  gpl1_last_error() returns a message for the last failure.
+ *   - Device-side waits are bounded by gpl1_params.timeout_ns; a wait that runs
+ *     out reports GPL1_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef GPL1_H
+#define GPL1_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gpl1_ctx gpl1_ctx; /* opaque: stream, device workspace, cached plans */
+
+typedef enum {
+  GPL1_OK = 0,
+  GPL1_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment, parameter           */
+  GPL1_ERR_CUDA = 2,          /* a CUDA runtime call failed                         */
+  GPL1_ERR_NOT_CONVERGED = 3, /* max_iter reached before the stop rule held         */
+  GPL1_ERR_LINESEARCH = 4,    /* Armijo backtracking cap reached (Alg. GP, Step 5)  */
+  GPL1_ERR_NONFINITE = 5,     /* f, a dot product or the steplength became NaN/inf  */
+  GPL1_ERR_TIMEOUT = 6,       /* a device-side wait exceeded timeout_ns             */
+  GPL1_ERR_UNSUPPORTED = 7    /* size beyond what this build handles                */
+} gpl1_status;
+
+typedef enum { GPL1_F64 = 0, GPL1_F32 = 1, GPL1_BF16 = 2 } gpl1_dtype;
+
+/* Why a solve stopped (gpl1_result.stop). */
+typedef enum {
+  GPL1_STOP_REL_GAP = 0,    /* (f(x) - f_star) / f_star <= tol                       */
+  GPL1_STOP_STATIONARY = 1, /* P(x - alpha g) == x exactly: stationary (Alg. GP, Step 2) */
+  GPL1_STOP_FW = 2,         /* Frank-Wolfe certificate (g^T x + rho ||g||_inf) <= tol (f - cert) */
+  GPL1_STOP_MAX_ITER = 3,
+  GPL1_STOP_ERROR = 4       /* see gpl1_result.status                                */
+} gpl1_stop;
+
+/* Stop rules (gpl1_params.stop_rule, a bit set; the solve stops at the first that holds). */
+#define GPL1_STOP_ON_REL_GAP 1 /* needs f_star > 0                                     */
+#define GPL1_STOP_ON_FW 2
+
+#define GPL1_DEBUG_UNREACHABLE_BARRIER 1
+
+typedef struct {
+  /* Algorithm GP (Sec. 3): Armijo parameters beta, theta in (0,1), memory M >= 1. */
+  double beta, theta;
+  int M;
+  /* Algorithm SS (Sec. 3): 0 < alpha_min < alpha_max, tau_1 in (0,1), M_alpha >= 0. */
+  double alpha_min, alpha_max, tau1;
+  int M_alpha;
+  /* stop rule */
+  double tol;          /* tolerance of the rules in stop_rule                          */
+  double f_star;       /* optimal value for GPL1_STOP_ON_REL_GAP (<= 0: unknown)       */
+  int stop_rule;       /* GPL1_STOP_ON_* bits; h == x always stops                     */
+  int max_iter;        /* iterations of Alg. GP                                        */
+  int max_backtracks;  /* trials of Alg. GP Step 5 before GPL1_ERR_LINESEARCH          */
+  int alpha0_rule;     /* 0: alpha_0 = 1/||P(x0 - g0)||_inf (Sec. 3, literal);
+                          1: alpha_0 = 1/||P(x0 - g0) - x0||_inf                      */
+  int x0_is_zero;      /* 1: ignore the contents of x and start from x0 = 0            */
+  int debug;           /* 0.  Bit GPL1_DEBUG_UNREACHABLE_BARRIER makes the group barrier
+                          of a multi-CTA solve wait for one arrival more than the group
+                          has, so the solve must end with GPL1_ERR_TIMEOUT after
+                          timeout_ns: a fault-free test of the bounded-wait path.      */
+  long long timeout_ns; /* bound on every device-side wait                             */
+} gpl1_params;
+
+typedef struct {
+  int status;          /* gpl1_status of this instance                                 */
+  int stop;            /* gpl1_stop                                                    */
+  int iters;           /* completed iterations of Alg. GP                              */
+  int backtracks;      /* total Armijo reductions lambda <- theta lambda               */
+  double f;            /* f at the returned x (from the exact quadratic expansion)      */
+  double rel_gap;      /* (f - f_star)/f_star if f_star > 0, else -1                    */
+  double fw_gap;       /* last Frank-Wolfe certificate g^T x + rho ||g||_inf (or -1)    */
+  double lambda;       /* last max|K^T (y - K x)| = ||g||_inf / 2 (relation of Sec. 1) */
+  double alpha;        /* last steplength alpha_k                                      */
+  double tau;          /* last projection threshold                                    */
+  double kernel_ms;    /* device time of the solver launch that produced this result
+                          (CUDA events on the context stream around the kernel)        */
+  int fail_site;       /* GPL1_ERR_TIMEOUT: which bounded wait gave up first (1 pass A
+                          box, 2 pass B box, 3 drain, 4 group barrier, 5 producer), or 0 */
+  int fail_iter;       /* iteration at which the solve ended                            */
+} gpl1_result;
+
+/* One instance of eq. 2 (device pointers).  x holds x0 on entry (projected onto
+ * the ball first if it lies outside, since Alg. GP starts in Omega) and the
+ * solution on exit. */
+typedef struct {
+  const void* K;
+  long long n, p, ldk;
+  const void* y;
+  double rho;     /* radius of the l1 ball, > 0                                        */
+  void* x;
+  double f_star;  /* optional per-instance optimal value (<= 0: use gpl1_params.f_star) */
+  double* trace;  /* optional device array of trace_cap rows of GPL1_TRACE_COLS doubles:
+                     row k = (f(x_k), alpha_k, lambda_k (0 if the line search failed),
+                     tau_{k+1} of Alg. SS, g_k^T d_k, ||K d_k||^2, ||d_k||^2,
+                     projection threshold, then the nanoseconds from the start of
+                     iteration k to the end of: pass A, its barrier, the projection
+                     phase, pass B, its barrier, the phase-P reductions, Alg. SS, the
+                     threshold search; then the number of threshold-search steps and
+                     seven clock stamps inside the search),
+                     written for k < trace_cap; NULL for none                        */
+  long long trace_cap;
+} gpl1_problem;
+
+#define GPL1_TRACE_COLS 24
+
+/* Create a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; 0 means the legacy default stream).  *out receives the
+ * context (NULL on failure).  The context allocates device workspace lazily and
+ * frees it in gpl1_destroy. */
+gpl1_status gpl1_create(gpl1_ctx** out, int device, void* cuda_stream);
+void gpl1_destroy(gpl1_ctx* ctx);
+gpl1_status gpl1_set_stream(gpl1_ctx* ctx, void* cuda_stream);
+const char* gpl1_last_error(const gpl1_ctx* ctx);
+
+/* Defaults of Sec. 3: M = 1, theta = 0.5, beta = 1e-4, alpha_min = 1e-10,
+ * alpha_max = 1e10, tau_1 = 0.5, M_alpha = 2, alpha_0 rule 0; plus tol = 1e-6,
+ * stop on the FW certificate, max_iter = 100000, max_backtracks = 100,
+ * timeout 10 s. */
+void gpl1_params_default(gpl1_params* prm);
+
+/* Euclidean projection onto {w : ||w||_1 <= rho_b} (the P_Omega of Alg. GP,
+ * Step 2), for `batch` segments of length p.  Segment b reads v + b*stride and
+ * writes out + b*stride (out may equal v).  rho points to `batch` doubles in
+ * host memory (rho_on_device = 0) or device memory (1).  Inside the ball the
+ * output equals the input bit for bit; otherwise out = sgn(v) max(|v| - tau, 0)
+ * with sum max(|v| - tau, 0) = rho, tau found by a radix select on |v| with
+ * exact fixed-point partial sums.  dtype GPL1_F64 or GPL1_F32.  tau_out, if not
+ * NULL, receives the `batch` thresholds (device pointer, double). */
+gpl1_status gpl1_project(gpl1_ctx* ctx, const void* v, void* out, gpl1_dtype dtype, long long p,
+                         long long batch, long long stride, const double* rho, int rho_on_device,
+                         double* tau_out);
+
+/* Solve one instance with Alg. GP + SS.  k_dtype is the element type of K
+ * (see the conventions above).  res: host pointer; the call synchronises the
+ * stream and fills it. */
+gpl1_status gpl1_solve(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype k_dtype,
+                       const gpl1_params* prm, gpl1_result* res);
+
+/* Solve `count` independent instances of possibly different n, p in one
+ * persistent launch.  probs: host array of descriptors (device pointers
+ * inside).  res: host array of `count` results; the call synchronises. */
+gpl1_status gpl1_solve_batched(gpl1_ctx* ctx, const gpl1_problem* probs, int count,
+                               gpl1_dtype k_dtype, const gpl1_params* prm, gpl1_result* res);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,225 @@
+"""Python binding of libgpl1 (include/gpl1.h): GPSS on one GB300 GPU.
+
+Argument marshalling only.  Tensors supply device pointers and PyTorch's
+current stream supplies the CUDA stream; every step of the method runs in the
+library's CUDA kernels.  There is no CPU path: if the compiled library is
+missing, every call raises.
+
+Names follow the C ABI: ``Context.project`` -> ``gpl1_project``,
+``Context.solve`` -> ``gpl1_solve``, ``Context.solve_batched`` ->
+``gpl1_solve_batched``, ``params_default`` -> ``gpl1_params_default``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libgpl1.so")
+
+F64, F32, BF16 = 0, 1, 2
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NOT_CONVERGED", 4: "LINESEARCH", 5: "NONFINITE",
+          6: "TIMEOUT", 7: "UNSUPPORTED"}
+STOP = {0: "rel_gap", 1: "stationary", 2: "fw", 3: "max_iter", 4: "error"}
+STOP_ON_REL_GAP, STOP_ON_FW = 1, 2
+DEBUG_UNREACHABLE_BARRIER = 1
+TRACE_COLS = 24
+# statuses that describe how a solve ended (reported in Result.status, not raised)
+ALGORITHMIC = (0, 3, 4, 5, 6)
+
+EXPORTS = ["gpl1_create", "gpl1_destroy", "gpl1_set_stream", "gpl1_last_error", "gpl1_params_default",
+           "gpl1_project", "gpl1_solve", "gpl1_solve_batched"]
+
+
+class Gpl1Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"gpl1 {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("theta", ctypes.c_double), ("M", ctypes.c_int),
+                ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double), ("tau1", ctypes.c_double),
+                ("M_alpha", ctypes.c_int), ("tol", ctypes.c_double), ("f_star", ctypes.c_double),
+                ("stop_rule", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_backtracks", ctypes.c_int),
+                ("alpha0_rule", ctypes.c_int), ("x0_is_zero", ctypes.c_int), ("debug", ctypes.c_int),
+                ("timeout_ns", ctypes.c_longlong)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("stop", ctypes.c_int), ("iters", ctypes.c_int),
+                ("backtracks", ctypes.c_int), ("f", ctypes.c_double), ("rel_gap", ctypes.c_double),
+                ("fw_gap", ctypes.c_double), ("lambda_", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("tau", ctypes.c_double), ("kernel_ms", ctypes.c_double), ("fail_site", ctypes.c_int),
+                ("fail_iter", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_void_p), ("n", ctypes.c_longlong), ("p", ctypes.c_longlong),
+                ("ldk", ctypes.c_longlong), ("y", ctypes.c_void_p), ("rho", ctypes.c_double),
+                ("x", ctypes.c_void_p), ("f_star", ctypes.c_double), ("trace", ctypes.c_void_p),
+                ("trace_cap", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+        L = ctypes.CDLL(LIB_PATH)
+        L.gpl1_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p]
+        L.gpl1_destroy.argtypes = [ctypes.c_void_p]
+        L.gpl1_destroy.restype = None
+        L.gpl1_set_stream.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.gpl1_last_error.argtypes = [ctypes.c_void_p]
+        L.gpl1_last_error.restype = ctypes.c_char_p
+        L.gpl1_params_default.argtypes = [ctypes.POINTER(Params)]
+        L.gpl1_params_default.restype = None
+        L.gpl1_project.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                   ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong,
+                                   ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        L.gpl1_solve.argtypes = [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.c_int,
+                                 ctypes.POINTER(Params), ctypes.POINTER(Result)]
+        L.gpl1_solve_batched.argtypes = [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(Params), ctypes.POINTER(Result)]
+        _lib = L
+    return _lib
+
+
+def params_default(**overrides) -> Params:
+    prm = Params()
+    lib().gpl1_params_default(ctypes.byref(prm))
+    for k, v in overrides.items():
+        if not hasattr(prm, k):
+            raise KeyError(k)
+        setattr(prm, k, v)
+    return prm
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype in (torch.bfloat16, torch.int16, torch.uint16):
+        return BF16
+    raise TypeError(f"unsupported K dtype {t.dtype}")
+
+
+def _stream_handle():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """A gpl1 context on one CUDA device (``gpl1_create``)."""
+
+    def __init__(self, device: int | None = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("gpl1 needs a CUDA GPU")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = ctypes.c_void_p()
+        st = lib().gpl1_create(ctypes.byref(h), self.device, _stream_handle())
+        if st != 0:
+            raise Gpl1Error(st, "gpl1_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gpl1_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != 0:
+            raise Gpl1Error(st, lib().gpl1_last_error(self._h).decode())
+
+    def _bind_stream(self):
+        lib().gpl1_set_stream(self._h, _stream_handle())
+
+    # ------------------------------------------------------------ project
+    def project(self, v, rho, out=None, tau=None):
+        """Project each row of v (p,) or (batch, p) onto {||w||_1 <= rho_b}; returns out."""
+        import torch
+        v2 = v if v.dim() == 2 else v.view(1, -1)
+        batch, p = v2.shape
+        if v2.stride(1) != 1:
+            raise ValueError("rows of v must be contiguous")
+        out = torch.empty_like(v2) if out is None else out.view(batch, p)
+        code = _dtype_code(v2)
+        if isinstance(rho, torch.Tensor) and rho.is_cuda:
+            rho_ptr, on_dev = ctypes.c_void_p(rho.data_ptr()), 1
+            keep = rho
+        else:
+            vals = [float(rho)] * batch if not isinstance(rho, (list, tuple, torch.Tensor)) else \
+                [float(r) for r in (rho.tolist() if isinstance(rho, torch.Tensor) else rho)]
+            keep = (ctypes.c_double * batch)(*vals)
+            rho_ptr, on_dev = ctypes.cast(keep, ctypes.c_void_p), 0
+        self._bind_stream()
+        st = lib().gpl1_project(self._h, ctypes.c_void_p(v2.data_ptr()), ctypes.c_void_p(out.data_ptr()), code,
+                                p, batch, v2.stride(0), rho_ptr, on_dev,
+                                ctypes.c_void_p(tau.data_ptr()) if tau is not None else None)
+        del keep
+        self._check(st)
+        return out.view_as(v)
+
+    # -------------------------------------------------------------- solve
+    @staticmethod
+    def make_problem(K, y, rho, x, p=None, f_star=-1.0, trace=None) -> Problem:
+        n, ldk = K.shape
+        return Problem(ctypes.c_void_p(K.data_ptr()), n, ldk if p is None else int(p), ldk,
+                       ctypes.c_void_p(y.data_ptr()), float(rho), ctypes.c_void_p(x.data_ptr()), float(f_star),
+                       ctypes.c_void_p(trace.data_ptr()) if trace is not None else None,
+                       trace.shape[0] if trace is not None else 0)
+
+    def solve(self, K, y, rho, x=None, p=None, params: Params | None = None, f_star: float = -1.0, trace=None):
+        """Solve min ||Kx - y||^2 s.t. ||x||_1 <= rho (gpl1_solve); x (device) is x0 in, solution out.
+
+        K: (n, ldk) tensor (float64, float32, or bfloat16 / int16 bit patterns); p <= ldk columns are used.
+        trace: optional float64 device tensor (cap, TRACE_COLS) receiving one row per iteration.
+        Returns (x, Result).
+        """
+        import torch
+        code = _dtype_code(K)
+        n, ldk = K.shape
+        p = ldk if p is None else int(p)
+        vdt = torch.float64 if code == F64 else torch.float32
+        prm = params_default() if params is None else params
+        if x is None:
+            x = torch.zeros(p, dtype=vdt, device=K.device)
+            prm = Params.from_buffer_copy(prm)
+            prm.x0_is_zero = 1
+        pr = self.make_problem(K, y, rho, x, p, f_star, trace)
+        res = Result()
+        self._bind_stream()
+        st = lib().gpl1_solve(self._h, ctypes.byref(pr), code, ctypes.byref(prm), ctypes.byref(res))
+        if st not in ALGORITHMIC:   # argument / CUDA errors raise; solver outcomes are in res.status
+            self._check(st)
+        return x, res
+
+    def solve_batched(self, problems: Sequence[Problem], dtype: int, params: Params | None = None):
+        """Solve independent instances in one persistent launch (gpl1_solve_batched); returns results."""
+        count = len(problems)
+        arr = (Problem * count)(*problems)
+        res = (Result * count)()
+        prm = params_default() if params is None else params
+        self._bind_stream()
+        st = lib().gpl1_solve_batched(self._h, arr, count, dtype, ctypes.byref(prm), res)
+        if st not in ALGORITHMIC:
+            self._check(st)
+        return list(res)

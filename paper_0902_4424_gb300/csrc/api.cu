@@ -1,0 +1,430 @@
+// C ABI of the gpl1 library: context, argument checks, device workspace,
+// TMA descriptors, launches.  See include/gpl1.h for the contract.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "launch.h"
+
+using namespace gpl1;
+
+struct gpl1_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  char err[512] = {0};
+  void* ws = nullptr;               // device workspace
+  size_t ws_bytes = 0;
+  gpl1_result* host_res = nullptr;  // pinned staging for results
+  size_t host_res_count = 0;
+  std::vector<uint8_t> host_stage;  // staging of descriptors (kept alive across async copies)
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};   // around the solver launch
+};
+
+namespace {
+
+gpl1_status fail(gpl1_ctx* c, gpl1_status st, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof c->err, fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+gpl1_status cuda_fail(gpl1_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, GPL1_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define GPL1_CUDA(call, what)                         \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int elem_size(int dt) { return dt == GPL1_F64 ? 8 : dt == GPL1_F32 ? 4 : 2; }
+int acc_size(int dt) { return dt == GPL1_F64 ? 8 : 4; }
+int rows_per_box(int dt) { return dt == GPL1_F64 ? Traits<GPL1_F64>::RB : dt == GPL1_F32 ? Traits<GPL1_F32>::RB : Traits<GPL1_BF16>::RB; }
+
+gpl1_status ensure_ws(gpl1_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return GPL1_OK;
+  if (ctx->ws) {
+    GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  const size_t want = align_up(bytes + bytes / 4, 1 << 20);
+  GPL1_CUDA(cudaMalloc(&ctx->ws, want), "cudaMalloc(workspace)");
+  ctx->ws_bytes = want;
+  return GPL1_OK;
+}
+
+gpl1_status ensure_host_res(gpl1_ctx* ctx, size_t count) {
+  if (count <= ctx->host_res_count) return GPL1_OK;
+  if (ctx->host_res) cudaFreeHost(ctx->host_res);
+  ctx->host_res = nullptr;
+  GPL1_CUDA(cudaMallocHost(&ctx->host_res, count * sizeof(gpl1_result)), "cudaMallocHost");
+  ctx->host_res_count = count;
+  return GPL1_OK;
+}
+
+gpl1_status check_params(gpl1_ctx* ctx, const gpl1_params* p) {
+  if (!p) return fail(ctx, GPL1_ERR_INVALID_ARG, "params is NULL");
+  if (!(p->beta > 0 && p->beta < 1) || !(p->theta > 0 && p->theta < 1))
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "beta and theta must lie in (0,1)");
+  if (p->M < 1 || p->M > kMaxM) return fail(ctx, GPL1_ERR_INVALID_ARG, "M must lie in [1,%d]", kMaxM);
+  if (p->M_alpha < 0 || p->M_alpha > kMaxMalpha)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "M_alpha must lie in [0,%d]", kMaxMalpha);
+  if (!(p->alpha_min > 0 && p->alpha_min < p->alpha_max) || !std::isfinite(p->alpha_max))
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "need 0 < alpha_min < alpha_max < inf");
+  if (!(p->tau1 > 0 && p->tau1 < 1)) return fail(ctx, GPL1_ERR_INVALID_ARG, "tau1 must lie in (0,1)");
+  if (!(p->tol >= 0) || !std::isfinite(p->tol)) return fail(ctx, GPL1_ERR_INVALID_ARG, "tol must be finite, >= 0");
+  if (p->max_iter < 1 || p->max_backtracks < 0) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad max_iter/max_backtracks");
+  if (p->timeout_ns <= 0) return fail(ctx, GPL1_ERR_INVALID_ARG, "timeout_ns must be > 0");
+  if (p->alpha0_rule != 0 && p->alpha0_rule != 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "alpha0_rule is 0 or 1");
+  return GPL1_OK;
+}
+
+gpl1_status check_problem(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, int idx) {
+  if (!pr) return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d is NULL", idx);
+  if (!pr->K || !pr->y || !pr->x) return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d: NULL K, y or x", idx);
+  if (pr->n < 1 || pr->p < 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d: n and p must be >= 1", idx);
+  if (pr->ldk < pr->p) return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d: ldk < p", idx);
+  if (!(pr->rho > 0) || !std::isfinite(pr->rho))
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d: rho must be finite and > 0", idx);
+  const int es = elem_size(dt);
+  if (reinterpret_cast<uintptr_t>(pr->K) % 16 != 0)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d: K must be 16-byte aligned", idx);
+  if ((pr->ldk * es) % 16 != 0)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d: ldk * sizeof(element) must be a multiple of 16", idx);
+  const int vs = dt == GPL1_F64 ? 8 : 4;
+  if (reinterpret_cast<uintptr_t>(pr->y) % vs || reinterpret_cast<uintptr_t>(pr->x) % vs)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d: x and y must be aligned to their element size", idx);
+  if (pr->p > static_cast<long long>(gpss_vmax(dt)) * kConsumers)
+    return fail(ctx, GPL1_ERR_UNSUPPORTED, "problem %d: p = %lld exceeds %d for this dtype", idx, pr->p,
+                gpss_vmax(dt) * kConsumers);
+  if (pr->n > (1LL << 30) || pr->ldk > (1LL << 31))
+    return fail(ctx, GPL1_ERR_UNSUPPORTED, "problem %d: n or ldk too large", idx);
+  return GPL1_OK;
+}
+
+gpl1_status encode_tmap(gpl1_ctx* ctx, CUtensorMap* map, const gpl1_problem* pr, int dt) {
+  if (!ctx->encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    GPL1_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q),
+              "cudaGetDriverEntryPointByVersion");
+    if (q != cudaDriverEntryPointSuccess || !fn)
+      return fail(ctx, GPL1_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    ctx->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const CUtensorMapDataType t = dt == GPL1_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                : dt == GPL1_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(pr->p), static_cast<cuuint64_t>(pr->n)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(pr->ldk) * elem_size(dt)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kBoxCols), static_cast<cuuint32_t>(rows_per_box(dt))};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = ctx->encode(map, t, 2, const_cast<void*>(pr->K), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, GPL1_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return GPL1_OK;
+}
+
+SolveParams to_kernel_params(const gpl1_params* p) {
+  SolveParams s;
+  s.beta = p->beta;
+  s.theta = p->theta;
+  s.alpha_min = p->alpha_min;
+  s.alpha_max = p->alpha_max;
+  s.tau1 = p->tau1;
+  s.tol = p->tol;
+  s.M = p->M;
+  s.M_alpha = p->M_alpha;
+  s.stop_rule = p->stop_rule;
+  s.max_iter = p->max_iter;
+  s.max_backtracks = p->max_backtracks;
+  s.alpha0_rule = p->alpha0_rule;
+  s.timeout_ns = p->timeout_ns;
+  s.debug = p->debug;
+  return s;
+}
+
+struct Sizes {
+  int NB, TC;
+  long long pp, nn, units;
+};
+Sizes sizes_of(const gpl1_problem* pr, int dt) {
+  Sizes s;
+  const int RB = rows_per_box(dt);
+  s.NB = static_cast<int>((pr->n + RB - 1) / RB);
+  s.TC = static_cast<int>((pr->p + kBoxCols - 1) / kBoxCols);
+  s.pp = static_cast<long long>(s.TC) * kBoxCols;
+  s.nn = static_cast<long long>(s.NB) * RB;
+  s.units = static_cast<long long>(s.NB) * s.TC;
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gpl1_params_default(gpl1_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->beta = 1e-4;
+  p->theta = 0.5;
+  p->M = 1;
+  p->alpha_min = 1e-10;
+  p->alpha_max = 1e10;
+  p->tau1 = 0.5;
+  p->M_alpha = 2;
+  p->tol = 1e-6;
+  p->f_star = -1.0;
+  p->stop_rule = GPL1_STOP_ON_REL_GAP | GPL1_STOP_ON_FW;
+  p->max_iter = 100000;
+  p->max_backtracks = 100;
+  p->alpha0_rule = 0;
+  p->x0_is_zero = 0;
+  p->timeout_ns = 10LL * 1000 * 1000 * 1000;
+}
+
+gpl1_status gpl1_create(gpl1_ctx** out, int device, void* stream) {
+  if (!out) return GPL1_ERR_INVALID_ARG;
+  *out = nullptr;
+  gpl1_ctx* ctx = new (std::nothrow) gpl1_ctx();
+  if (!ctx) return GPL1_ERR_CUDA;
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return GPL1_ERR_CUDA;
+  }
+  *out = ctx;
+  return GPL1_OK;
+}
+
+void gpl1_destroy(gpl1_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->ws) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws);
+  }
+  if (ctx->host_res) cudaFreeHost(ctx->host_res);
+  for (cudaEvent_t e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+gpl1_status gpl1_set_stream(gpl1_ctx* ctx, void* stream) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return GPL1_OK;
+}
+
+const char* gpl1_last_error(const gpl1_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+gpl1_status gpl1_project(gpl1_ctx* ctx, const void* v, void* out, gpl1_dtype dtype, long long p, long long batch,
+                         long long stride, const double* rho, int rho_on_device, double* tau_out) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  if (!v || !out || !rho) return fail(ctx, GPL1_ERR_INVALID_ARG, "NULL pointer");
+  if (dtype != GPL1_F64 && dtype != GPL1_F32) return fail(ctx, GPL1_ERR_INVALID_ARG, "dtype must be F64 or F32");
+  if (p < 1 || batch < 1 || stride < p) return fail(ctx, GPL1_ERR_INVALID_ARG, "need p >= 1, batch >= 1, stride >= p");
+  if (batch > 2147483647LL) return fail(ctx, GPL1_ERR_UNSUPPORTED, "batch too large");
+  if (p > project_max_p(dtype))
+    return fail(ctx, GPL1_ERR_UNSUPPORTED, "p = %lld exceeds %lld", p, project_max_p(dtype));
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const double* rho_dev = rho;
+  if (!rho_on_device) {
+    for (long long b = 0; b < batch; ++b)
+      if (!(rho[b] > 0) || !std::isfinite(rho[b])) return fail(ctx, GPL1_ERR_INVALID_ARG, "rho[%lld] must be > 0", b);
+    gpl1_status st = ensure_ws(ctx, static_cast<size_t>(batch) * sizeof(double));
+    if (st) return st;
+    GPL1_CUDA(cudaMemcpyAsync(ctx->ws, rho, static_cast<size_t>(batch) * sizeof(double), cudaMemcpyHostToDevice,
+                              ctx->stream),
+              "cudaMemcpyAsync(rho)");
+    rho_dev = static_cast<const double*>(ctx->ws);
+  }
+  GPL1_CUDA(launch_project(dtype, v, out, p, batch, stride, rho_dev, tau_out, ctx->stream), "project kernel");
+  if (!rho_on_device) GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  return GPL1_OK;
+}
+
+namespace {
+
+// Launch `count` instances.  group > 1: one instance over `group` CTAs
+// (cooperative); group == 1: persistent CTAs pulling instances from a queue.
+gpl1_status run(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
+                gpl1_result* res) {
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  // largest-first order for the queue (the longest instances start first)
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  if (count > 1)
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return probs[a].n * probs[a].p > probs[b].n * probs[b].p;
+    });
+  const int as = acc_size(dt);
+  // workspace: [counters 256][descs][results][tmaps][gbuf/kbuf per instance]
+  const size_t off_desc = 256;
+  const size_t off_res = align_up(off_desc + sizeof(InstDesc) * count, 256);
+  const size_t off_tmap = align_up(off_res + sizeof(gpl1_result) * count, 256);
+  const bool batched = count > 1;
+  size_t off_bufs = align_up(off_tmap + (batched ? sizeof(CUtensorMap) * count : 0), 256);
+  std::vector<size_t> off_g(count), off_k(count), off_p(count);
+  const int max_group = batched ? 1 : ctx->num_sms * 4;
+  size_t cur = off_bufs;
+  for (int q = 0; q < count; ++q) {
+    const Sizes s = sizes_of(&probs[q], dt);
+    off_g[q] = cur;
+    cur = align_up(cur + 3 * s.pp * as, 256);
+    off_k[q] = cur;
+    cur = align_up(cur + 4 * s.nn * as, 256);
+    off_p[q] = cur;   // pass-B partials: 4 doubles per CTA of the group
+    cur = align_up(cur + 32 * static_cast<size_t>(max_group), 256);
+  }
+  gpl1_status st = ensure_ws(ctx, cur);
+  if (st) return st;
+  st = ensure_host_res(ctx, count);
+  if (st) return st;
+  uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
+
+  // host staging of descriptors and tensor maps
+  ctx->host_stage.assign(off_bufs - off_desc, 0);
+  InstDesc* hd = reinterpret_cast<InstDesc*>(ctx->host_stage.data());
+  CUtensorMap* ht = reinterpret_cast<CUtensorMap*>(ctx->host_stage.data() + (off_tmap - off_desc));
+  gpl1_result* hr = reinterpret_cast<gpl1_result*>(ctx->host_stage.data() + (off_res - off_desc));
+  for (int q = 0; q < count; ++q) {   // overwritten by the kernel; stays if an instance never ran
+    hr[q].status = GPL1_ERR_TIMEOUT;
+    hr[q].stop = GPL1_STOP_ERROR;
+  }
+  CUtensorMap tmap0;
+  std::memset(&tmap0, 0, sizeof tmap0);
+  for (int q = 0; q < count; ++q) {
+    const int src = order[q];
+    const gpl1_problem& pr = probs[src];
+    InstDesc& d = hd[q];
+    d.y = pr.y;
+    d.x = pr.x;
+    d.rho = pr.rho;
+    d.f_star = pr.f_star > 0 ? pr.f_star : prm->f_star;
+    d.n = static_cast<int>(pr.n);
+    d.p = static_cast<int>(pr.p);
+    d.x0_zero = prm->x0_is_zero ? 1 : 0;
+    d.pad = 0;
+    d.gbuf = ws + off_g[src];
+    d.kbuf = ws + off_k[src];
+    d.res = reinterpret_cast<gpl1_result*>(ws + off_res) + src;
+    d.trace = pr.trace;
+    d.trace_cap = pr.trace ? pr.trace_cap : 0;
+    d.pbuf = ws + off_p[src];
+    if (batched) {
+      st = encode_tmap(ctx, &ht[q], &pr, dt);
+      d.tmap = ws + off_tmap + sizeof(CUtensorMap) * q;
+    } else {
+      st = encode_tmap(ctx, &tmap0, &pr, dt);
+      d.tmap = nullptr;
+    }
+    if (st) return st;
+  }
+  if (prm->x0_is_zero)   // x0 = 0: the iterate buffer must start at zero
+    for (int q = 0; q < count; ++q)
+      GPL1_CUDA(cudaMemsetAsync(probs[q].x, 0, static_cast<size_t>(probs[q].p) * (dt == GPL1_F64 ? 8 : 4),
+                                ctx->stream),
+                "cudaMemsetAsync(x)");
+  GPL1_CUDA(cudaMemsetAsync(ws, 0, 256, ctx->stream), "cudaMemsetAsync");
+  GPL1_CUDA(cudaMemsetAsync(ws + off_bufs, 0, cur - off_bufs, ctx->stream), "cudaMemsetAsync");
+  GPL1_CUDA(cudaMemcpyAsync(ws + off_desc, ctx->host_stage.data(), off_bufs - off_desc, cudaMemcpyHostToDevice,
+                            ctx->stream),
+            "cudaMemcpyAsync(desc)");
+
+  KArgs ka;
+  ka.desc = reinterpret_cast<const InstDesc*>(ws + off_desc);
+  ka.count = count;
+  ka.queue = reinterpret_cast<unsigned*>(ws + 0);
+  ka.bar = reinterpret_cast<unsigned*>(ws + 64);
+  ka.err = reinterpret_cast<int*>(ws + 128);
+  ka.prm = to_kernel_params(prm);
+
+  int occ = 0;
+  GPL1_CUDA(cudaFuncSetAttribute(gpss_kernel_ptr(dt), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(gpss_smem_bytes(dt))),
+            "cudaFuncSetAttribute");
+  GPL1_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gpss_kernel_ptr(dt), kThreads, gpss_smem_bytes(dt)),
+            "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (occ < 1) return fail(ctx, GPL1_ERR_CUDA, "solver kernel does not fit on an SM");
+  if (!ctx->ev[0]) {
+    GPL1_CUDA(cudaEventCreate(&ctx->ev[0]), "cudaEventCreate");
+    GPL1_CUDA(cudaEventCreate(&ctx->ev[1]), "cudaEventCreate");
+  }
+  GPL1_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream), "cudaEventRecord");
+  if (!batched) {
+    const Sizes s = sizes_of(&probs[0], dt);
+    const long long G = std::min<long long>(static_cast<long long>(ctx->num_sms) * occ, s.units);
+    ka.group = static_cast<int>(G);
+    GPL1_CUDA(launch_gpss(dt, ka, tmap0, ka.group, G > 1, ctx->stream), "solver launch");
+  } else {
+    ka.group = 1;
+    const int grid = std::min(ctx->num_sms * occ, count);
+    GPL1_CUDA(launch_gpss(dt, ka, tmap0, grid, false, ctx->stream), "solver launch");
+  }
+  GPL1_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream), "cudaEventRecord");
+  GPL1_CUDA(cudaMemcpyAsync(ctx->host_res, ws + off_res, sizeof(gpl1_result) * count, cudaMemcpyDeviceToHost,
+                            ctx->stream),
+            "cudaMemcpyAsync(result)");
+  GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "solver");
+  std::memcpy(res, ctx->host_res, sizeof(gpl1_result) * count);
+  float ms = 0.f;
+  GPL1_CUDA(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]), "cudaEventElapsedTime");
+  for (int q = 0; q < count; ++q) res[q].kernel_ms = ms;
+  int worst = GPL1_OK;
+  for (int q = 0; q < count; ++q)
+    if (res[q].status != GPL1_OK && res[q].status != GPL1_ERR_NOT_CONVERGED) worst = res[q].status;
+  if (worst != GPL1_OK) return fail(ctx, static_cast<gpl1_status>(worst), "an instance failed (status %d)", worst);
+  return GPL1_OK;
+}
+
+}  // namespace
+
+gpl1_status gpl1_solve(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype dt, const gpl1_params* prm,
+                       gpl1_result* res) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  if (dt != GPL1_F64 && dt != GPL1_F32 && dt != GPL1_BF16) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad dtype");
+  if (!res) return fail(ctx, GPL1_ERR_INVALID_ARG, "result is NULL");
+  gpl1_status st = check_params(ctx, prm);
+  if (st) return st;
+  st = check_problem(ctx, prob, dt, 0);
+  if (st) return st;
+  return run(ctx, prob, 1, dt, prm, res);
+}
+
+gpl1_status gpl1_solve_batched(gpl1_ctx* ctx, const gpl1_problem* probs, int count, gpl1_dtype dt,
+                               const gpl1_params* prm, gpl1_result* res) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  if (dt != GPL1_F64 && dt != GPL1_F32 && dt != GPL1_BF16) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad dtype");
+  if (!probs || !res || count < 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "need probs, res and count >= 1");
+  gpl1_status st = check_params(ctx, prm);
+  if (st) return st;
+  for (int q = 0; q < count; ++q) {
+    st = check_problem(ctx, &probs[q], dt, q);
+    if (st) return st;
+  }
+  return run(ctx, probs, count, dt, prm, res);
+}
+
+}  // extern "C"

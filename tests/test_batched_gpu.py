@@ -1,0 +1,66 @@
+"""gpl1_solve_batched: many independent instances of uneven n, p in one
+persistent launch, each checked against the FP64 oracle at the same bars as
+single solves (relative objective gap <= 1e-6, feasibility)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_0902_4424_gb300 as pkg
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def upload(prob):
+    if prob.dtype == W.DT_BF16:
+        K = torch.from_numpy(prob.K.view(np.int16)).to(DEV)
+    else:
+        K = torch.from_numpy(prob.K).to(DEV)
+    y = torch.from_numpy(prob.y).to(DEV)
+    x = torch.zeros(prob.p, dtype=torch.float64 if prob.dtype == W.DT_F64 else torch.float32, device=DEV)
+    return K, y, x
+
+
+def run_batch(ctx, probs, dtype, fstars, tol=5e-7):
+    keep, descs = [], []
+    for pr, fs in zip(probs, fstars):
+        K, y, x = upload(pr)
+        keep.append((K, y, x))
+        descs.append(pkg.Context.make_problem(K, y, pr.rho, x, pr.p, fs))
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=tol, x0_is_zero=1, max_iter=20000)
+    res = ctx.solve_batched(descs, dtype, prm)
+    torch.cuda.synchronize()
+    return [k[2].double().cpu().numpy() for k in keep], res
+
+
+@pytest.mark.parametrize("dtype", [W.DT_BF16, W.DT_F32])
+def test_ragged_batch_vs_oracle(gpu_ctx, dtype):
+    rng = np.random.default_rng(17)
+    sizes = [int(v) for v in rng.integers(16, 420, size=40)]
+    sizes[:4] = [1, 2, 31, 419]                     # degenerate and ragged rows
+    probs = [W.gaussian(n, 4 * n, max(1, n // 20), dtype=dtype, seed=1000 + i, law="pm1")
+             for i, n in enumerate(sizes)]
+    refs = [oracle.reference_solve(p)[1].f for p in probs]
+    xs, res = run_batch(gpu_ctx, probs, dtype, refs)
+    for pr, x, r, fs in zip(probs, xs, res, refs):
+        f = oracle.objective(pr, x)
+        assert r.status == 0, (pr.n, r.as_dict(), f, fs)
+        assert (f - fs) <= 1e-6 * fs + 1e-12, (pr.n, f, fs)
+        assert np.abs(x).sum() <= pr.rho * (1 + 1e-6)
+
+
+def test_ragged_batch_config3_shapes(gpu_ctx):
+    """Instances drawn like the 512-instance ragged batch (n in [128, 2048],
+    p = 4n, BF16 K, +-1 signals with n/20 non-zeros): the first 16 of them,
+    each against the oracle's optimum."""
+    sizes = W.ragged_sizes(16)
+    probs = [W.ragged_instance(i, n) for i, n in enumerate(sizes)]
+    refs = [oracle.floor_solve(pr)[1].f for pr in probs]
+    xs, res = run_batch(gpu_ctx, probs, W.DT_BF16, refs)
+    for pr, x, r, fs in zip(probs, xs, res, refs):
+        gap = (oracle.objective(pr, x) - fs) / fs
+        assert r.status == 0 and r.stop == 0, (pr.n, r.as_dict(), gap)
+        assert gap <= 1e-6
+        assert np.abs(x).sum() <= pr.rho * (1 + 1e-6)
