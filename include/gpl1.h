@@ -54,7 +54,7 @@ typedef enum { GPL1_F64 = 0, GPL1_F32 = 1, GPL1_BF16 = 2 } gpl1_dtype;
 
 /* Why a solve stopped (gpl1_result.stop). */
 typedef enum {
-  GPL1_STOP_REL_GAP = 0,    /* (f(x) - f_star) / f_star <= tol                       */
+  GPL1_STOP_REL_GAP = 0,    /* f(x) - f_star <= tol max(f_star, tol ||y||^2)         */
   GPL1_STOP_STATIONARY = 1, /* P(x - alpha g) == x exactly: stationary (Alg. GP, Step 2) */
   GPL1_STOP_FW = 2,         /* Frank-Wolfe certificate (g^T x + rho ||g||_inf) <= tol (f - cert) */
   GPL1_STOP_MAX_ITER = 3,

@@ -146,7 +146,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, uint64_
       "l"(tmap), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
       : "memory");
 }
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
+// Named barrier 1 over the consumer warps (the producer warp never joins).
+// The non-aligned form: it is defined when the threads of a warp reach it at
+// different times (lead-only sections, loops with uneven trip counts right
+// before it), which the aligned bar.sync leaves undefined; with bar.sync the
+// FP64 solver stalled in such a section.
+__device__ __forceinline__ void consumer_sync() { asm volatile("barrier.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
 
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");

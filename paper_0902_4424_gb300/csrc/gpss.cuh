@@ -104,6 +104,7 @@ struct SSState {
 
 struct Uni {
   double alpha, tau, lam, f_cur, gd, dd, gmax;
+  double gap_den;   // denominator of the relative-gap stop: max(f*, tol ||y||^2)
   SSState<float> ssf;
   SSState<double> ssd;
   float ah, al, th, tl, lf;   // alpha, tau as float pairs and lam as float, for the FP32 pipe
@@ -271,6 +272,11 @@ struct Consumer {
   __device__ static S s_of(A v) {
     if constexpr (kF64) return v;
     else return F2{v, 0.f};
+  }
+  // acc + a*b; for float data the product is exact and the sum compensated
+  __device__ static void s_fma(S& acc, A a, A b) {
+    if constexpr (kF64) acc = fma(a, b, acc);
+    else acc = f2_fma(acc, a, b);
   }
 
   // ---- pipeline
@@ -449,7 +455,11 @@ struct Consumer {
   // setup (gk == null): d = 0 and x = S_tau(x_mem) (the projected x0).
   __device__ void pass_b(const A* gk, const Dir& dir, A* kout, double* part) {
     A dv[8], xv[8];
-    A sgd = 0, sdd = 0;
+    // g^T d is a sum of terms of both signs whose total goes to 0 as the
+    // iteration converges, while the Armijo test needs its sign right: it is
+    // accumulated compensated.  ||d||^2 has terms of one sign only.
+    S sgd{};
+    A sdd = 0;
     unsigned snz = 0;
     int cur = -1;
     for (int u = u1 - 1; u >= u0; --u) {
@@ -468,7 +478,7 @@ struct Consumer {
               const A gj = gk[col];
               dj = dir.d(xj, gj);
               if (owns) {
-                sgd = vfma(gj, dj, sgd);
+                s_fma(sgd, gj, dj);
                 sdd = vfma(dj, dj, sdd);
                 snz |= dj != A(0) ? 1u : 0u;
               }
@@ -506,7 +516,7 @@ struct Consumer {
       release();
     }
     if (part) {
-      S v[2] = {s_of(sgd), s_of(sdd)};
+      S v[2] = {sgd, s_of(sdd)};
       lead_reduce<2>(v, snz, sm.sc);
       if (tid == 0) {
         double* o = part + 4 * cta;
@@ -755,7 +765,7 @@ struct Consumer {
     }
     u.f_cur = fnext;
     u.iters = k + 1;
-    if ((P.stop_rule & GPL1_STOP_ON_REL_GAP) && D.f_star > 0.0 && fnext - D.f_star <= P.tol * D.f_star) {
+    if ((P.stop_rule & GPL1_STOP_ON_REL_GAP) && D.f_star > 0.0 && fnext - D.f_star <= P.tol * u.gap_den) {
       u.stop = GPL1_STOP_REL_GAP;
       u.done = 1;
     } else if (u.iters >= P.max_iter) {
@@ -831,9 +841,15 @@ struct Consumer {
       S o[3];
       line_scalars(kbuf + 2 * nn, o);
       if (tid == 0) u.f_cur = as_double(o[0]);
-    } else {
-      const double f0 = sum_sq_y();
-      if (tid == 0) u.f_cur = f0;
+    }
+    {
+      // ||y||^2 = f(0).  With f* ~ 0 (an exact fit) a relative gap cannot be
+      // resolved, so the gap is then measured against tol ||y||^2 instead.
+      const double yy = sum_sq_y();
+      if (tid == 0) {
+        if (D.x0_zero) u.f_cur = yy;
+        u.gap_den = fmax(D.f_star, P.tol * yy);
+      }
     }
     if (tid == 0)
       for (int q = 0; q < kMaxM; ++q) u.fhist[q] = u.f_cur;
