@@ -104,8 +104,10 @@ double ora_project_l1(const double* v, double* out, long p, double rho) {
   double* u = (double*)malloc((size_t)p * sizeof(double));
   for (long i = 0; i < p; ++i) u[i] = fabs(v[i]);
   qsort(u, (size_t)p, sizeof(double), cmp_desc);
-  double S = 0.0, tau = 0.0;
-  for (long j = 1; j <= p; ++j) {
+  /* j = 1 always qualifies (u_1 - (u_1 - rho) = rho > 0); start from it so
+     that a rho below the rounding unit of u_1 still gives a threshold. */
+  double S = u[0], tau = u[0] - rho;
+  for (long j = 2; j <= p; ++j) {
     S += u[j - 1];
     double t = (S - rho) / (double)j;
     if (u[j - 1] > t) tau = t;
