@@ -81,7 +81,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
@@ -90,7 +90,14 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self, start: bool):
+        """Wall-clock bounds of the timed region (samples outside it are ignored)."""
+        if start:
+            self.t0 = time.monotonic()
+        else:
+            self.t1 = time.monotonic()
 
     def __exit__(self, *exc):
         if self.proc:
@@ -103,7 +110,11 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0, t1 = getattr(self, "t0", None), getattr(self, "t1", None)
+        # nvidia-smi reports each sample a little after taking it: keep the
+        # samples that arrive inside the region or within one period after it
+        picked = [ln for t, ln in self.lines if t0 is None or (t0 <= t <= t1 + 0.1)]
+        for ln in picked:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -118,7 +129,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "interval_ms": 50}
 
 
 # -------------------------------------------------------------- CPU oracle
@@ -193,9 +204,11 @@ def run_ours(args, rank, world, local_rank):
             raise RuntimeError(f"solve failed: {res.as_dict()}")
         return res
 
+    clk = ClockSampler(local_rank).__enter__()   # running before the timed region starts
     for _ in range(args.warmup):
         solve()
     torch.cuda.synchronize()
+    time.sleep(0.3)
 
     # ---- device-timed steps (inputs resident in HBM, L2 flushed between steps)
     stream = torch.cuda.current_stream()
@@ -204,15 +217,18 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clk:
-        for s in range(args.steps):
-            flush.fill_(float(s))
-            evs[s][0].record(stream)
-            res = solve()
-            evs[s][1].record(stream)
-            kernel_ms.append(res.kernel_ms)
-            iters.append(res.iters)
-        torch.cuda.synchronize()
+    clk.mark(True)
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        evs[s][0].record(stream)
+        res = solve()
+        evs[s][1].record(stream)
+        kernel_ms.append(res.kernel_ms)
+        iters.append(res.iters)
+    torch.cuda.synchronize()
+    clk.mark(False)
+    time.sleep(0.15)
+    clk.__exit__(None, None, None)
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
@@ -316,7 +332,7 @@ def kernel_fingerprint():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=10.0)

@@ -62,7 +62,7 @@ typedef enum {
 } gpl1_stop;
 
 /* Stop rules (gpl1_params.stop_rule, a bit set; the solve stops at the first that holds). */
-#define GPL1_STOP_ON_REL_GAP 1 /* needs f_star > 0                                     */
+#define GPL1_STOP_ON_REL_GAP 1 /* needs f_star >= 0                                    */
 #define GPL1_STOP_ON_FW 2
 
 #define GPL1_DEBUG_UNREACHABLE_BARRIER 1
@@ -76,7 +76,7 @@ typedef struct {
   int M_alpha;
   /* stop rule */
   double tol;          /* tolerance of the rules in stop_rule                          */
-  double f_star;       /* optimal value for GPL1_STOP_ON_REL_GAP (<= 0: unknown)       */
+  double f_star;       /* optimal value for GPL1_STOP_ON_REL_GAP (< 0: unknown)        */
   int stop_rule;       /* GPL1_STOP_ON_* bits; h == x always stops                     */
   int max_iter;        /* iterations of Alg. GP                                        */
   int max_backtracks;  /* trials of Alg. GP Step 5 before GPL1_ERR_LINESEARCH          */
@@ -117,7 +117,7 @@ typedef struct {
   const void* y;
   double rho;     /* radius of the l1 ball, > 0                                        */
   void* x;
-  double f_star;  /* optional per-instance optimal value (<= 0: use gpl1_params.f_star) */
+  double f_star;  /* optional per-instance optimal value (< 0: use gpl1_params.f_star) */
   double* trace;  /* optional device array of trace_cap rows of GPL1_TRACE_COLS doubles:
                      row k = (f(x_k), alpha_k, lambda_k (0 if the line search failed),
                      tau_{k+1} of Alg. SS, g_k^T d_k, ||K d_k||^2, ||d_k||^2,

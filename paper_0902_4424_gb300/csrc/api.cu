@@ -294,7 +294,7 @@ gpl1_status run(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, con
     off_g[q] = cur;
     cur = align_up(cur + 3 * s.pp * as, 256);
     off_k[q] = cur;
-    cur = align_up(cur + 4 * s.nn * as, 256);
+    cur = align_up(cur + 2 * kbuf_stride(s.nn, as), 256);
     off_p[q] = cur;   // pass-B partials: 4 doubles per CTA of the group
     cur = align_up(cur + 32 * static_cast<size_t>(max_group), 256);
   }
@@ -322,7 +322,7 @@ gpl1_status run(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, con
     d.y = pr.y;
     d.x = pr.x;
     d.rho = pr.rho;
-    d.f_star = pr.f_star > 0 ? pr.f_star : prm->f_star;
+    d.f_star = pr.f_star >= 0 ? pr.f_star : prm->f_star;
     d.n = static_cast<int>(pr.n);
     d.p = static_cast<int>(pr.p);
     d.x0_zero = prm->x0_is_zero ? 1 : 0;

@@ -163,13 +163,19 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 __device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
 
-// Two-element reduction into global memory (pass B writes (Kd_i, Kx_i) pairs).
-__device__ __forceinline__ void red_add2(float* addr, float a, float b) {
+// Reductions into global memory (no return value: compiled as red, not atom).
+__device__ __forceinline__ void red_add(float* addr, float a) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(a) : "memory");
+}
+__device__ __forceinline__ void red_add(double* addr, double a) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(addr), "d"(a) : "memory");
+}
+__device__ __forceinline__ void red_add2(float* addr, float a, float b) {   // 8-byte aligned pair
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
 }
 __device__ __forceinline__ void red_add2(double* addr, double a, double b) {
-  atomicAdd(addr, a);
-  atomicAdd(addr + 1, b);
+  red_add(addr, a);
+  red_add(addr + 1, b);
 }
 
 // ------------------------------------------------------- shared scratch

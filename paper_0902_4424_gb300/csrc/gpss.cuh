@@ -42,16 +42,28 @@
 
 namespace gpl1 {
 
+// Per-instance buffer of the pass-B products, two of them (iterations
+// alternate): [(K d, K x) pairs: 2 nn values of the accumulation type]
+// [K x: nn doubles].  Float data near the stop sum K x compensated into the
+// FP64 array instead of the pair (r = K x - y cancels most of its digits near
+// the solution); K d shrinks with d and always stays in the pair.
+__host__ __device__ inline size_t kbuf_pair_bytes(long long nn, int acc_bytes) {
+  return (static_cast<size_t>(nn) * 2 * acc_bytes + 255) & ~static_cast<size_t>(255);
+}
+__host__ __device__ inline size_t kbuf_stride(long long nn, int acc_bytes) {
+  return kbuf_pair_bytes(nn, acc_bytes) + ((static_cast<size_t>(nn) * 8 + 255) & ~static_cast<size_t>(255));
+}
+
 struct InstDesc {
   const void* y;        // V[n]
   void* x;              // V[p]: x0 in, solution out
   double rho;
-  double f_star;        // <= 0: unknown
+  double f_star;        // < 0: unknown
   int n, p;
   int x0_zero;
   int pad;
   void* gbuf;           // A[3][pp], zeroed before launch
-  void* kbuf;           // A[2][nn][2], zeroed before launch
+  void* kbuf;           // 2 x kbuf_stride(nn) bytes, zeroed before launch
   gpl1_result* res;     // device result slot
   const void* tmap;     // CUtensorMap of K in global memory, or null for the kernel argument
   double* trace;        // optional per-iteration record (GPL1_TRACE_COLS doubles per row)
@@ -82,6 +94,10 @@ enum { kSiteNone = 0, kSitePassA = 1, kSitePassB = 2, kSiteDrain = 3, kSiteGroup
 
 // Bound on waits for TMA copies that are already in flight (drain, quiesce).
 constexpr uint64_t kInflightNs = 2000000000ull;
+// Pass B sums K x with compensated arithmetic once the distance to the
+// requested stop is below this many times the tolerance (FP32 sums of K x
+// carry about 1e-7 relative noise into f).
+constexpr double kAccGapFactor = 100.0;
 
 // SolveParams.debug bit: the group barrier waits for one arrival more than the
 // group has, so every wait runs out.  Exercises the bounded-wait error path.
@@ -105,6 +121,13 @@ struct SSState {
 struct Uni {
   double alpha, tau, lam, f_cur, gd, dd, gmax;
   double gap_den;   // denominator of the relative-gap stop: max(f*, tol ||y||^2)
+  // x_k as stored times this factor is the iterate: 1, or slightly below 1 when
+  // rounding in the update x + lam d left ||x||_1 above rho (the iterate must
+  // stay in the ball for d to be a descent direction)
+  double xscale_d;
+  float xscale_f;
+  int acc_kx;       // pass B sums K x with compensated arithmetic (near the stop)
+  int kmode[2];     // acc_kx of the pass B that filled each pass-B buffer
   SSState<float> ssf;
   SSState<double> ssd;
   float ah, al, th, tl, lf;   // alpha, tau as float pairs and lam as float, for the FP32 pipe
@@ -254,7 +277,7 @@ struct Consumer {
   unsigned& epoch;
   const int cta, G, tid, lane, warp, n, p, NB, TC, u0, u1, pp, nn;
   A* gbuf;
-  A* kbuf;
+  uint8_t* kbuf;
   const V* y;
   V* x;
   int status = GPL1_OK;
@@ -266,8 +289,23 @@ struct Consumer {
         TC((D_.p + kBoxCols - 1) / kBoxCols),
         u0(static_cast<int>(static_cast<long long>(NB) * TC * cta_ / G_)),
         u1(static_cast<int>(static_cast<long long>(NB) * TC * (cta_ + 1) / G_)),
-        pp(TC * kBoxCols), nn(NB * RB), gbuf(static_cast<A*>(D_.gbuf)), kbuf(static_cast<A*>(D_.kbuf)),
+        pp(TC * kBoxCols), nn(NB * RB), gbuf(static_cast<A*>(D_.gbuf)), kbuf(static_cast<uint8_t*>(D_.kbuf)),
         y(static_cast<const V*>(D_.y)), x(static_cast<V*>(D_.x)) {}
+
+  __device__ A xscale() const {
+    if constexpr (kF64) return sm.uni.xscale_d;
+    else return sm.uni.xscale_f;
+  }
+  __device__ A* kp_of(int b) const { return reinterpret_cast<A*>(kbuf + b * kbuf_stride(nn, sizeof(A))); }
+  __device__ double* kx_of(int b) const {
+    return reinterpret_cast<double*>(kbuf + b * kbuf_stride(nn, sizeof(A)) + kbuf_pair_bytes(nn, sizeof(A)));
+  }
+  // r_i = (K x)_i - y_i from buffer b, in the working type (FP64 for the
+  // compensated form, whose K x is in the FP64 array)
+  __device__ A resid(const A* kp, const double* kx64, bool comp, int i) const {
+    if constexpr (kF64) return kp[2 * i + 1] - y[i];
+    else return comp ? static_cast<float>(kx64[i] - static_cast<double>(y[i])) : kp[2 * i + 1] - y[i];
+  }
 
   __device__ static S s_of(A v) {
     if constexpr (kF64) return v;
@@ -409,7 +447,7 @@ struct Consumer {
     consumer_sync();
   }
 
-  __device__ void pass_a(const A* kprev, A lp, A* gout) {
+  __device__ void pass_a(const A* kp, const double* kx64, bool comp, A lp, A* gout) {
     A acc[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) acc[e] = 0;
@@ -427,7 +465,7 @@ struct Consumer {
       A rv = 0;
       if (lane < RPW) {
         const int i = b * RB + warp + kConsumerWarps * lane;
-        if (i < n) rv = 2 * (kprev[2 * i + 1] - static_cast<A>(y[i]) + lp * kprev[2 * i]);
+        if (i < n) rv = 2 * (resid(kp, kx64, comp, i) + lp * kp[2 * i]);
       }
       const uint8_t* st = wait_full(kSitePassA);
       if (!st) {
@@ -447,19 +485,25 @@ struct Consumer {
     if (cur >= 0) flush_a(cur, acc, gout);
   }
 
-  // ---- pass B: kout[2i] += (K d)_i, kout[2i+1] += (K x)_i, with
+  // ---- pass B: kd[i] += (K d)_i, kx[i] += (K x)_i, with
   // d_j = P(x - alpha g)_j - x_j rebuilt per strip from x, g (no d vector in
   // memory).  The CTA that owns row box 0 of a strip also accumulates
   // g^T d, ||d||^2 and "d != 0" over the strip's columns (each column counted
   // once in the group) and publishes its totals in part[cta].
   // setup (gk == null): d = 0 and x = S_tau(x_mem) (the projected x0).
-  __device__ void pass_b(const A* gk, const Dir& dir, A* kout, double* part) {
+  // (K x)_i is summed without rounding error on float data: each product
+  // K_ij x_j is split exactly into a float pair (FMA), the lane's terms and
+  // the warp's lanes are added with error-free two-sums, and the pair is
+  // added to the FP64 total in global memory.
+  __device__ void pass_b(const A* gk, const Dir& dir, A* kp, double* kx64, double* part) {
     A dv[8], xv[8];
     // g^T d is a sum of terms of both signs whose total goes to 0 as the
     // iteration converges, while the Armijo test needs its sign right: it is
     // accumulated compensated.  ||d||^2 has terms of one sign only.
     S sgd{};
     A sdd = 0;
+    const A xsc = gk ? xscale() : A(1);
+    const bool acc = sm.uni.acc_kx != 0;
     unsigned snz = 0;
     int cur = -1;
     for (int u = u1 - 1; u >= u0; --u) {
@@ -473,7 +517,7 @@ struct Consumer {
           const int col = s * kBoxCols + LC::col(lane, e);
           A xj = 0, dj = 0;
           if (col < p) {
-            xj = static_cast<A>(x[col]);
+            xj = static_cast<A>(x[col]) * xsc;
             if (gk) {
               const A gj = gk[col];
               dj = dir.d(xj, gj);
@@ -499,19 +543,63 @@ struct Consumer {
       for (int q = 0; q < RPW; ++q) {
         A kv[8];
         load_row8<DT>(st + (warp + kConsumerWarps * q) * (kBoxCols * T::ES), lane, kv);
-        A pd = 0, px = 0;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          pd = vfma(kv[e], dv[e], pd);
-          px = vfma(kv[e], xv[e], px);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          pd += __shfl_xor_sync(0xffffffffu, pd, o);
-          px += __shfl_xor_sync(0xffffffffu, px, o);
-        }
         const int i = b * RB + warp + kConsumerWarps * q;
-        if (lane == 0 && i < n) red_add2(kout + 2 * i, pd, px);
+        A pd = 0;
+        if constexpr (kF64) {
+          double px = 0;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            pd = fma(kv[e], dv[e], pd);
+            px = fma(kv[e], xv[e], px);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            pd += __shfl_xor_sync(0xffffffffu, pd, o);
+            px += __shfl_xor_sync(0xffffffffu, px, o);
+          }
+          if (lane == 0 && i < n) red_add2(kp + 2 * i, pd, px);
+        } else {
+          float sh = 0.f, sl = 0.f;   // (K x) partial as an unevaluated pair
+          if (acc) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              pd = fmaf(kv[e], dv[e], pd);
+              const float pr = __fmul_rn(kv[e], xv[e]);
+              const float pe = fmaf(kv[e], xv[e], -pr);   // K_ij x_j - pr, exact
+              const F2 t = two_sum(sh, pr);
+              sh = t.hi;
+              sl = __fadd_rn(sl, __fadd_rn(pe, t.lo));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              pd += __shfl_xor_sync(0xffffffffu, pd, o);
+              const float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+              const float ol = __shfl_xor_sync(0xffffffffu, sl, o);
+              const F2 t = two_sum(sh, oh);
+              sh = t.hi;
+              sl = __fadd_rn(__fadd_rn(sl, ol), t.lo);
+            }
+          } else {   // far from the stop: plain FP32 sums
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              pd = fmaf(kv[e], dv[e], pd);
+              sh = fmaf(kv[e], xv[e], sh);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              pd += __shfl_xor_sync(0xffffffffu, pd, o);
+              sh += __shfl_xor_sync(0xffffffffu, sh, o);
+            }
+          }
+          if (lane == 0 && i < n) {
+            if (acc) {
+              red_add(kp + 2 * i, pd);
+              red_add(kx64 + i, static_cast<double>(sh) + static_cast<double>(sl));
+            } else {
+              red_add2(kp + 2 * i, pd, sh);
+            }
+          }
+        }
       }
       release();
     }
@@ -567,11 +655,11 @@ struct Consumer {
 
   // ---- phase L scalars: f = ||Kx - y||^2, a = r^T Kd, b = ||Kd||^2 (r = Kx - y),
   // summed into thread 0 (lead_reduce).
-  __device__ void line_scalars(const A* kk, S (&o)[3]) {
+  __device__ void line_scalars(const A* kp, const double* kx64, bool comp, S (&o)[3]) {
     if constexpr (kF64) {
       double v[3] = {0, 0, 0};
       for (int i = tid; i < n; i += kConsumers) {
-        const double kd = kk[2 * i], r = kk[2 * i + 1] - y[i];
+        const double kd = kp[2 * i], r = kp[2 * i + 1] - y[i];
         v[0] = fma(r, r, v[0]);
         v[1] = fma(r, kd, v[1]);
         v[2] = fma(kd, kd, v[2]);
@@ -582,8 +670,15 @@ struct Consumer {
     } else {
       F2 v[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
       for (int i = tid; i < n; i += kConsumers) {
-        const float kd = kk[2 * i];
-        const F2 r = two_sum(kk[2 * i + 1], -static_cast<float>(y[i]));
+        const float kd = kp[2 * i];
+        F2 r;
+        if (comp) {   // r_i in FP64, then as a float pair
+          const double rd = kx64[i] - static_cast<double>(y[i]);
+          const float rh = static_cast<float>(rd);
+          r = F2{rh, static_cast<float>(rd - static_cast<double>(rh))};
+        } else {
+          r = two_sum(kp[2 * i + 1], -static_cast<float>(y[i]));
+        }
         v[0] = f2_fma(v[0], r.hi, r.hi + 2.f * r.lo);
         v[1] = f2_fma(v[1], r.hi + r.lo, kd);
         v[2] = f2_fma(v[2], kd, kd);
@@ -596,18 +691,79 @@ struct Consumer {
     lead_reduce<3>(o, dummy, sm.sc);
   }
 
-  __device__ void zero_slices(A* gz, A* kz) {
+  __device__ void zero_slices(A* gz, int kb) {
     const int j0 = static_cast<int>(static_cast<long long>(pp) * cta / G);
     const int j1 = static_cast<int>(static_cast<long long>(pp) * (cta + 1) / G);
     for (int j = j0 + tid; j < j1; j += kConsumers) gz[j] = 0;
-    const int i0 = static_cast<int>(2LL * nn * cta / G), i1 = static_cast<int>(2LL * nn * (cta + 1) / G);
-    for (int i = i0 + tid; i < i1; i += kConsumers) kz[i] = 0;
+    A* const kz = kp_of(kb);
+    double* const xz = kx_of(kb);
+    const int i0 = static_cast<int>(static_cast<long long>(nn) * cta / G);
+    const int i1 = static_cast<int>(static_cast<long long>(nn) * (cta + 1) / G);
+    for (int i = i0 + tid; i < i1; i += kConsumers) {
+      kz[2 * i] = 0;
+      kz[2 * i + 1] = 0;
+      xz[i] = 0.0;
+    }
+  }
+
+  // Float data near the stop: tau again, on the active set A the search found
+  // (|v| > tau), from x and g themselves rather than from v = x - alpha g as
+  // rounded into shared memory.  With s = sgn v, the direction of pass B gives
+  // h = x + d with sum_A |h_j| = sum_A s_j x_j - alpha sum_A s_j g_j - |A| tau,
+  // so this tau makes ||h||_1 = rho to float-pair accuracy.  The rounding of v
+  // (half an ulp of each |v_j|) would otherwise leave ||h||_1 - rho of the
+  // order of the decrease the Armijo test has to see near the solution.
+  __device__ void refine_tau(const A* gk, int neu, float& th, float& tl) {
+    const V* const xs = sm.xs;
+    const TauPair tp{th, tl};
+    const A xsc = xscale();
+    S v[3] = {S{}, S{}, S{}};
+#pragma unroll 4
+    for (int e = 0; e < VMAX; ++e) {
+      if (e >= neu) break;
+      const int j = tid + e * kConsumers;
+      const float vv = xs[e * kConsumers + tid];
+      if (j < p && !tp.below(fabsf(vv))) {
+        const float sg = vv > 0.f ? 1.f : -1.f;
+        v[0] = f2_add(v[0], sg * (static_cast<A>(x[j]) * xsc));
+        v[1] = f2_add(v[1], sg * gk[j]);
+        v[2] = f2_add(v[2], 1.f);
+      }
+    }
+    unsigned dummy = 0;
+    lead_reduce<3>(v, dummy, sm.sc);
+    if (tid == 0) {
+      const Uni& u = sm.uni;
+      const F2 sx = v[0], sgs = v[1];
+      const float c = v[2].hi;   // |A| (an integer below 2^24: exact)
+      // alpha * S_g with alpha = ah + al, the leading product split exactly
+      const float ph = __fmul_rn(u.ah, sgs.hi);
+      const float pl = fmaf(u.ah, sgs.hi, -ph) + fmaf(u.ah, sgs.lo, u.al * sgs.hi);
+      F2 t = f2_add(sx, F2{-ph, -pl});
+      t = f2_add(t, F2{-u.rho_p.hi, -u.rho_p.lo});
+      // t / c as a float pair: the remainder of the leading quotient is exact
+      const float q1 = __fdiv_rn(t.hi, c);
+      const float rem = fmaf(-q1, c, t.hi) + t.lo;
+      const F2 q = two_sum(q1, __fdiv_rn(rem, c));
+      if (c > 0.f && q.hi > 0.f) {
+        sm.sc.tp[2] = q.hi;
+        sm.sc.tp[3] = q.lo;
+      } else {   // keep the search's value
+        sm.sc.tp[2] = th;
+        sm.sc.tp[3] = tl;
+      }
+    }
+    consumer_sync();
+    th = sm.sc.tp[2];
+    tl = sm.sc.tp[3];
+    consumer_sync();
   }
 
   // xs := x - a g for every column this thread holds (x from shared memory
   // when from_smem, else from global; g from global, in chunks so the loads
   // of a chunk are in flight together).
   __device__ void stage_v(const A* gk, V av, bool from_smem, int neu) {
+    const V xsc = static_cast<V>(xscale());
     V* const xs = sm.xs;
     constexpr int CH = 7;
 #pragma unroll
@@ -624,7 +780,7 @@ struct Consumer {
       for (int i = 0; i < CH; ++i) {
         const int e = c0 + i;
         if (e >= VMAX || e >= neu) break;
-        const V xe = from_smem ? xs[e * kConsumers + tid] : xv[i];
+        const V xe = (from_smem ? xs[e * kConsumers + tid] : xv[i]) * xsc;
         xs[e * kConsumers + tid] = vfma(-av, gv[i], xe);
       }
     }
@@ -659,6 +815,23 @@ struct Consumer {
     if (P.M_alpha > 0) st.a2win[0] = a2_this;
     if (st.a2cnt < P.M_alpha) ++st.a2cnt;
     return alpha;
+  }
+
+  // Feasibility of the stored x_k (lead thread).  In exact arithmetic every
+  // iterate of Alg. GP lies in the ball (x_k + lam d_k with lam <= 1 is a
+  // convex combination of feasible points); rounding in the update can leave
+  // ||x||_1 a few ulps above rho.  The iterate is then x_k scaled back onto
+  // the ball, with a factor rounded down so the scaled vector is feasible.
+  __device__ void set_xscale(double l1) {   // FP64 data
+    Uni& u = sm.uni;
+    u.xscale_d = l1 > D.rho ? (D.rho / l1) * (1.0 - 0x1p-50) : 1.0;
+  }
+  __device__ void set_xscale(const F2& l1) {   // float data: float work only
+    Uni& u = sm.uni;
+    const F2 rp = u.rho_p;
+    // l1 - rho, exact to a few ulps of rho (the high parts cancel exactly)
+    const float ex = (l1.hi - rp.hi) + (l1.lo - rp.lo);
+    u.xscale_f = ex > 0.f ? __fdiv_rd(rp.hi, l1.hi) * (1.f - 0x1p-21f) : 1.f;
   }
 
   // Publish alpha_k (lead thread): a float pair for the FP32 pipe and the bound
@@ -765,7 +938,10 @@ struct Consumer {
     }
     u.f_cur = fnext;
     u.iters = k + 1;
-    if ((P.stop_rule & GPL1_STOP_ON_REL_GAP) && D.f_star > 0.0 && fnext - D.f_star <= P.tol * u.gap_den) {
+    if ((P.stop_rule & GPL1_STOP_ON_REL_GAP) && D.f_star >= 0.0 &&
+        fnext - D.f_star <= kAccGapFactor * P.tol * u.gap_den)
+      u.acc_kx = 1;
+    if ((P.stop_rule & GPL1_STOP_ON_REL_GAP) && D.f_star >= 0.0 && fnext - D.f_star <= P.tol * u.gap_den) {
       u.stop = GPL1_STOP_REL_GAP;
       u.done = 1;
     } else if (u.iters >= P.max_iter) {
@@ -817,6 +993,12 @@ struct Consumer {
       u.status = GPL1_OK;
       u.done = 0;
       u.psteps = 0;
+      u.xscale_d = 1.0;
+      u.xscale_f = 1.f;
+      // with no target to approach, every pass B sums K x compensated
+      u.acc_kx = (P.stop_rule & (GPL1_STOP_ON_REL_GAP | GPL1_STOP_ON_FW)) ? 0 : 1;
+      u.kmode[0] = 0;
+      u.kmode[1] = kF64 ? 0 : u.acc_kx;   // the setup pass B (x0 given) fills buffer 1
     }
     consumer_sync();
 
@@ -831,7 +1013,7 @@ struct Consumer {
       const SmemAcc<V, VMAX> acc0{xs, neu};
       const TauResult t0 = block_l1_tau_fixed_point<V>(acc0, rho, u.rho_p, 0.f, sm.u.proj, sm.sc);
       const Dir dir0(t0.tau, t0.th, t0.tl, t0.inside);
-      pass_b(nullptr, dir0, kbuf + 2 * nn, nullptr);
+      pass_b(nullptr, dir0, kp_of(1), kx_of(1), nullptr);
       if (!group_sync()) goto finish;
       if (!t0.inside) {   // write the projected x0 only after every CTA has read x0
         const int j0 = static_cast<int>(static_cast<long long>(p) * cta / G);
@@ -839,7 +1021,7 @@ struct Consumer {
         for (int j = j0 + tid; j < j1; j += kConsumers) x[j] = static_cast<V>(dir0.proj(static_cast<A>(x[j])));
       }
       S o[3];
-      line_scalars(kbuf + 2 * nn, o);
+      line_scalars(kp_of(1), kx_of(1), u.kmode[1] != 0, o);
       if (tid == 0) u.f_cur = as_double(o[0]);
     }
     {
@@ -858,10 +1040,10 @@ struct Consumer {
     for (int k = 0;; ++k) {
       A* const gk = gbuf + (k % 3) * pp;
       A* const gprev = gbuf + ((k + 2) % 3) * pp;
-      A* const kcur = kbuf + (k & 1) * 2 * nn;
       if (tid == 0 && D.trace) u.ts[5] = globaltimer();
       // ---------------- pass A: g_k = 2 K^T r_k
-      pass_a(kbuf + ((k + 1) & 1) * 2 * nn, kF64 ? static_cast<A>(u.lam) : static_cast<A>(u.lf), gk);
+      pass_a(kp_of((k + 1) & 1), kx_of((k + 1) & 1), u.kmode[(k + 1) & 1] != 0,
+             kF64 ? static_cast<A>(u.lam) : static_cast<A>(u.lf), gk);
       if (tid == 0 && D.trace) u.ts[0] = globaltimer();
       if (!group_sync()) break;
       if (tid == 0 && D.trace) u.ts[1] = globaltimer();
@@ -869,6 +1051,7 @@ struct Consumer {
       // ---------------- phase P: z^T z, g^T x, ||g||_inf; Alg. SS; threshold
       {
         A part2[2] = {0, 0}, pm = 0;
+        S l1{};   // ||x_k||_1, compensated: it is compared with rho to a few ulps
         constexpr int CH = 7;   // loads of a chunk are issued together, then stored
 #pragma unroll
         for (int c0 = 0; c0 < VMAX; c0 += CH) {
@@ -892,28 +1075,33 @@ struct Consumer {
             }
             xs[e * kConsumers + tid] = xv[i];
             part2[1] = vfma(gv[i], static_cast<A>(xv[i]), part2[1]);
+            if constexpr (kF64) l1 += fabs(xv[i]);
+            else l1 = f2_add(l1, fabsf(xv[i]));
             pm = vmax(pm, vabs(gv[i]));
           }
         }
-        S red[2] = {s_of(part2[0]), s_of(part2[1])};
+        S red[3] = {s_of(part2[0]), s_of(part2[1]), l1};
         unsigned mx = kF64 ? __float_as_uint(static_cast<float>(pm) * 1.0000002f) : __float_as_uint(static_cast<float>(pm));
-        lead_reduce<2>(red, mx, sm.sc);
+        lead_reduce<3>(red, mx, sm.sc);
         double gmax64 = 0.0;
         if constexpr (kF64) gmax64 = block_max_nonneg(static_cast<double>(pm), sm.sc);
         if (tid == 0 && D.trace) u.ts[6] = globaltimer();
         if (tid == 0) {
           u.gmaxf = __uint_as_float(mx);
           u.set_gx(red[1]);
+          set_xscale(red[2]);
           if constexpr (kF64) u.gmax = gmax64;
           if (P.stop_rule & GPL1_STOP_ON_FW) {   // FP64 only when this rule is on
             const double gmax = kF64 ? gmax64 : static_cast<double>(u.gmaxf);
             const double fw = as_double(red[1]) + rho * gmax;
+            if (fw <= kAccGapFactor * P.tol * (u.f_cur - fw)) u.acc_kx = 1;
             if (fw <= P.tol * (u.f_cur - fw)) {
               u.stop = GPL1_STOP_FW;
               u.iters = k;
               u.done = 1;
             }
           }
+          u.kmode[k & 1] = u.acc_kx;   // the form of this iteration's pass B
           if (!u.done && k > 0) {
             if constexpr (kF64) set_alpha(ss_step(u.ssd, red[0]));
             else set_alpha(ss_step(u.ssf, red[0].hi + red[0].lo));
@@ -957,24 +1145,28 @@ struct Consumer {
         // projection h = P(x - alpha g): its threshold (the direction d = h - x is formed in pass B)
         const SmemAcc<V, VMAX> vacc{xs, neu};
         const TauResult tv = block_l1_tau_fixed_point<V>(vacc, rho, u.rho_p, u.th, sm.u.proj, sm.sc, u.vbound);
+        float th = tv.th, tl = tv.tl;
+        if constexpr (!kF64) {
+          if (u.acc_kx && !tv.inside) refine_tau(gk, neu, th, tl);
+        }
         if (tid == 0) {
           if (D.trace) u.ts[8] = globaltimer();
           u.psteps = sm.sc.flags[2];
           for (int q = 0; q < 8; ++q) u.tt[q] = sm.sc.tt[q];
-          u.tau = tv.inside ? 0.0 : tv.tau;
-          u.th = tv.th;
-          u.tl = tv.tl;
+          u.tau = tv.inside ? 0.0 : (kF64 ? tv.tau : static_cast<double>(th) + static_cast<double>(tl));
+          u.th = th;
+          u.tl = tl;
           u.inside = tv.inside;
         }
       }
       // the pass-A reductions of k+1 and the pass-B ones of k+1 go to buffers
       // nobody reads any more: clear this CTA's slices
-      zero_slices(gbuf + ((k + 1) % 3) * pp, kbuf + ((k + 1) & 1) * 2 * nn);
+      zero_slices(gbuf + ((k + 1) % 3) * pp, (k + 1) & 1);
       consumer_sync();
 
       if (tid == 0 && D.trace) u.ts[2] = globaltimer();
       // ---------------- pass B: [K d_k, K x_k], g^T d, ||d||^2
-      pass_b(gk, Dir(u), kcur, part);
+      pass_b(gk, Dir(u), kp_of(k & 1), kx_of(k & 1), part);
       if (tid == 0 && D.trace) u.ts[3] = globaltimer();
       if (!group_sync()) break;
       if (tid == 0 && D.trace) u.ts[4] = globaltimer();
@@ -982,7 +1174,7 @@ struct Consumer {
       // ---------------- phase L
       {
         S ls[3];
-        line_scalars(kcur, ls);
+        line_scalars(kp_of(k & 1), kx_of(k & 1), u.kmode[k & 1] != 0, ls);
         S gd, dd;
         unsigned nz;
         if (warp == 0) reduce_parts(part, gd, dd, nz);
@@ -1010,8 +1202,9 @@ struct Consumer {
         const Dir dir(u);
         const int j0 = static_cast<int>(static_cast<long long>(p) * cta / G);
         const int j1 = static_cast<int>(static_cast<long long>(p) * (cta + 1) / G);
+        const A xsc = xscale();
         for (int j = j0 + tid; j < j1; j += kConsumers) {
-          const A xj = static_cast<A>(x[j]);
+          const A xj = static_cast<A>(x[j]) * xsc;
           x[j] = static_cast<V>(vfma(la, dir.d(xj, gk[j]), xj));
         }
         if (u.done) break;
