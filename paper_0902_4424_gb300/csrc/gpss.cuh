@@ -302,9 +302,10 @@ struct Consumer {
   }
   // r_i = (K x)_i - y_i from buffer b, in the working type (FP64 for the
   // compensated form, whose K x is in the FP64 array)
-  __device__ A resid(const A* kp, const double* kx64, bool comp, int i) const {
-    if constexpr (kF64) return kp[2 * i + 1] - y[i];
-    else return comp ? static_cast<float>(kx64[i] - static_cast<double>(y[i])) : kp[2 * i + 1] - y[i];
+  template <bool COMP>
+  __device__ A resid(const A* kp, const double* kx64, int i) const {
+    if constexpr (kF64 || !COMP) return kp[2 * i + 1] - static_cast<A>(y[i]);
+    else return static_cast<float>(kx64[i] - static_cast<double>(y[i]));
   }
 
   __device__ static S s_of(A v) {
@@ -447,7 +448,8 @@ struct Consumer {
     consumer_sync();
   }
 
-  __device__ void pass_a(const A* kp, const double* kx64, bool comp, A lp, A* gout) {
+  template <bool COMP>
+  __device__ void pass_a(const A* kp, const double* kx64, A lp, A* gout) {
     A acc[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) acc[e] = 0;
@@ -465,7 +467,7 @@ struct Consumer {
       A rv = 0;
       if (lane < RPW) {
         const int i = b * RB + warp + kConsumerWarps * lane;
-        if (i < n) rv = 2 * (resid(kp, kx64, comp, i) + lp * kp[2 * i]);
+        if (i < n) rv = 2 * (resid<COMP>(kp, kx64, i) + lp * kp[2 * i]);
       }
       const uint8_t* st = wait_full(kSitePassA);
       if (!st) {
@@ -495,6 +497,7 @@ struct Consumer {
   // K_ij x_j is split exactly into a float pair (FMA), the lane's terms and
   // the warp's lanes are added with error-free two-sums, and the pair is
   // added to the FP64 total in global memory.
+  template <bool ACC>
   __device__ void pass_b(const A* gk, const Dir& dir, A* kp, double* kx64, double* part) {
     A dv[8], xv[8];
     // g^T d is a sum of terms of both signs whose total goes to 0 as the
@@ -503,7 +506,7 @@ struct Consumer {
     S sgd{};
     A sdd = 0;
     const A xsc = gk ? xscale() : A(1);
-    const bool acc = sm.uni.acc_kx != 0;
+    constexpr bool acc = ACC;
     unsigned snz = 0;
     int cur = -1;
     for (int u = u1 - 1; u >= u0; --u) {
@@ -560,7 +563,7 @@ struct Consumer {
           if (lane == 0 && i < n) red_add2(kp + 2 * i, pd, px);
         } else {
           float sh = 0.f, sl = 0.f;   // (K x) partial as an unevaluated pair
-          if (acc) {
+          if constexpr (acc) {
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               pd = fmaf(kv[e], dv[e], pd);
@@ -592,7 +595,7 @@ struct Consumer {
             }
           }
           if (lane == 0 && i < n) {
-            if (acc) {
+            if constexpr (acc) {
               red_add(kp + 2 * i, pd);
               red_add(kx64 + i, static_cast<double>(sh) + static_cast<double>(sl));
             } else {
@@ -655,7 +658,8 @@ struct Consumer {
 
   // ---- phase L scalars: f = ||Kx - y||^2, a = r^T Kd, b = ||Kd||^2 (r = Kx - y),
   // summed into thread 0 (lead_reduce).
-  __device__ void line_scalars(const A* kp, const double* kx64, bool comp, S (&o)[3]) {
+  template <bool COMP>
+  __device__ void line_scalars(const A* kp, const double* kx64, S (&o)[3]) {
     if constexpr (kF64) {
       double v[3] = {0, 0, 0};
       for (int i = tid; i < n; i += kConsumers) {
@@ -672,7 +676,7 @@ struct Consumer {
       for (int i = tid; i < n; i += kConsumers) {
         const float kd = kp[2 * i];
         F2 r;
-        if (comp) {   // r_i in FP64, then as a float pair
+        if constexpr (COMP) {   // r_i in FP64, then as a float pair
           const double rd = kx64[i] - static_cast<double>(y[i]);
           const float rh = static_cast<float>(rd);
           r = F2{rh, static_cast<float>(rd - static_cast<double>(rh))};
@@ -704,6 +708,51 @@ struct Consumer {
       kz[2 * i + 1] = 0;
       xz[i] = 0.0;
     }
+  }
+
+  // Phase P's pass over x_k and g_k: z^T z (z = g_k - g_{k-1}), g^T x, max |g|
+  // into the first two sums and mx; stores x_k into shared memory.  Near the
+  // stop (L1) also ||x_k||_1, compensated, for the feasibility check.
+  template <bool L1>
+  __device__ void phase_p_sums(const A* gk, const A* gprev, int k, int neu, S (&red)[3], unsigned& mx, A& pm) {
+    V* const xs = sm.xs;
+    A part2[2] = {0, 0};
+    pm = 0;
+    S l1{};
+    constexpr int CH = 7;   // loads of a chunk are issued together, then stored
+#pragma unroll
+    for (int c0 = 0; c0 < VMAX; c0 += CH) {
+      A gv[CH], gp[CH];
+      V xv[CH];
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        const int e = c0 + i, j = tid + e * kConsumers;
+        const bool ok = e < VMAX && e < neu && j < p;
+        gv[i] = ok ? gk[j] : A(0);
+        xv[i] = ok ? x[j] : V(0);
+        gp[i] = (ok && k > 0) ? gprev[j] : A(0);
+      }
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        const int e = c0 + i;
+        if (e >= VMAX || e >= neu) break;
+        if (k > 0) {
+          const A z = gv[i] - gp[i];
+          part2[0] = vfma(z, z, part2[0]);
+        }
+        xs[e * kConsumers + tid] = xv[i];
+        part2[1] = vfma(gv[i], static_cast<A>(xv[i]), part2[1]);
+        if constexpr (L1) {
+          if constexpr (kF64) l1 += fabs(xv[i]);
+          else l1 = f2_add(l1, fabsf(xv[i]));
+        }
+        pm = vmax(pm, vabs(gv[i]));
+      }
+    }
+    red[0] = s_of(part2[0]);
+    red[1] = s_of(part2[1]);
+    red[2] = l1;
+    mx = kF64 ? __float_as_uint(static_cast<float>(pm) * 1.0000002f) : __float_as_uint(static_cast<float>(pm));
   }
 
   // Float data near the stop: tau again, on the active set A the search found
@@ -1013,7 +1062,8 @@ struct Consumer {
       const SmemAcc<V, VMAX> acc0{xs, neu};
       const TauResult t0 = block_l1_tau_fixed_point<V>(acc0, rho, u.rho_p, 0.f, sm.u.proj, sm.sc);
       const Dir dir0(t0.tau, t0.th, t0.tl, t0.inside);
-      pass_b(nullptr, dir0, kp_of(1), kx_of(1), nullptr);
+      if (u.kmode[1]) pass_b<true>(nullptr, dir0, kp_of(1), kx_of(1), nullptr);
+      else pass_b<false>(nullptr, dir0, kp_of(1), kx_of(1), nullptr);
       if (!group_sync()) goto finish;
       if (!t0.inside) {   // write the projected x0 only after every CTA has read x0
         const int j0 = static_cast<int>(static_cast<long long>(p) * cta / G);
@@ -1021,7 +1071,8 @@ struct Consumer {
         for (int j = j0 + tid; j < j1; j += kConsumers) x[j] = static_cast<V>(dir0.proj(static_cast<A>(x[j])));
       }
       S o[3];
-      line_scalars(kp_of(1), kx_of(1), u.kmode[1] != 0, o);
+      if (u.kmode[1]) line_scalars<true>(kp_of(1), kx_of(1), o);
+      else line_scalars<false>(kp_of(1), kx_of(1), o);
       if (tid == 0) u.f_cur = as_double(o[0]);
     }
     {
@@ -1042,46 +1093,23 @@ struct Consumer {
       A* const gprev = gbuf + ((k + 2) % 3) * pp;
       if (tid == 0 && D.trace) u.ts[5] = globaltimer();
       // ---------------- pass A: g_k = 2 K^T r_k
-      pass_a(kp_of((k + 1) & 1), kx_of((k + 1) & 1), u.kmode[(k + 1) & 1] != 0,
-             kF64 ? static_cast<A>(u.lam) : static_cast<A>(u.lf), gk);
+      {
+        const A lp = kF64 ? static_cast<A>(u.lam) : static_cast<A>(u.lf);
+        if (!kF64 && u.kmode[(k + 1) & 1]) pass_a<true>(kp_of((k + 1) & 1), kx_of((k + 1) & 1), lp, gk);
+        else pass_a<false>(kp_of((k + 1) & 1), kx_of((k + 1) & 1), lp, gk);
+      }
       if (tid == 0 && D.trace) u.ts[0] = globaltimer();
       if (!group_sync()) break;
       if (tid == 0 && D.trace) u.ts[1] = globaltimer();
 
       // ---------------- phase P: z^T z, g^T x, ||g||_inf; Alg. SS; threshold
       {
-        A part2[2] = {0, 0}, pm = 0;
-        S l1{};   // ||x_k||_1, compensated: it is compared with rho to a few ulps
-        constexpr int CH = 7;   // loads of a chunk are issued together, then stored
-#pragma unroll
-        for (int c0 = 0; c0 < VMAX; c0 += CH) {
-          A gv[CH], gp[CH];
-          V xv[CH];
-#pragma unroll
-          for (int i = 0; i < CH; ++i) {
-            const int e = c0 + i, j = tid + e * kConsumers;
-            const bool ok = e < VMAX && e < neu && j < p;
-            gv[i] = ok ? gk[j] : A(0);
-            xv[i] = ok ? x[j] : V(0);
-            gp[i] = (ok && k > 0) ? gprev[j] : A(0);
-          }
-#pragma unroll
-          for (int i = 0; i < CH; ++i) {
-            const int e = c0 + i;
-            if (e >= VMAX || e >= neu) break;
-            if (k > 0) {
-              const A z = gv[i] - gp[i];
-              part2[0] = vfma(z, z, part2[0]);
-            }
-            xs[e * kConsumers + tid] = xv[i];
-            part2[1] = vfma(gv[i], static_cast<A>(xv[i]), part2[1]);
-            if constexpr (kF64) l1 += fabs(xv[i]);
-            else l1 = f2_add(l1, fabsf(xv[i]));
-            pm = vmax(pm, vabs(gv[i]));
-          }
-        }
-        S red[3] = {s_of(part2[0]), s_of(part2[1]), l1};
-        unsigned mx = kF64 ? __float_as_uint(static_cast<float>(pm) * 1.0000002f) : __float_as_uint(static_cast<float>(pm));
+        S red[3];
+        unsigned mx;
+        A pm;
+        const bool near = u.acc_kx != 0;
+        if (near) phase_p_sums<true>(gk, gprev, k, neu, red, mx, pm);
+        else phase_p_sums<false>(gk, gprev, k, neu, red, mx, pm);
         lead_reduce<3>(red, mx, sm.sc);
         double gmax64 = 0.0;
         if constexpr (kF64) gmax64 = block_max_nonneg(static_cast<double>(pm), sm.sc);
@@ -1089,7 +1117,7 @@ struct Consumer {
         if (tid == 0) {
           u.gmaxf = __uint_as_float(mx);
           u.set_gx(red[1]);
-          set_xscale(red[2]);
+          if (near) set_xscale(red[2]);
           if constexpr (kF64) u.gmax = gmax64;
           if (P.stop_rule & GPL1_STOP_ON_FW) {   // FP64 only when this rule is on
             const double gmax = kF64 ? gmax64 : static_cast<double>(u.gmaxf);
@@ -1166,7 +1194,8 @@ struct Consumer {
 
       if (tid == 0 && D.trace) u.ts[2] = globaltimer();
       // ---------------- pass B: [K d_k, K x_k], g^T d, ||d||^2
-      pass_b(gk, Dir(u), kp_of(k & 1), kx_of(k & 1), part);
+      if (!kF64 && u.kmode[k & 1]) pass_b<true>(gk, Dir(u), kp_of(k & 1), kx_of(k & 1), part);
+      else pass_b<false>(gk, Dir(u), kp_of(k & 1), kx_of(k & 1), part);
       if (tid == 0 && D.trace) u.ts[3] = globaltimer();
       if (!group_sync()) break;
       if (tid == 0 && D.trace) u.ts[4] = globaltimer();
@@ -1174,7 +1203,8 @@ struct Consumer {
       // ---------------- phase L
       {
         S ls[3];
-        line_scalars(kp_of(k & 1), kx_of(k & 1), u.kmode[k & 1] != 0, ls);
+        if (!kF64 && u.kmode[k & 1]) line_scalars<true>(kp_of(k & 1), kx_of(k & 1), ls);
+        else line_scalars<false>(kp_of(k & 1), kx_of(k & 1), ls);
         S gd, dd;
         unsigned nz;
         if (warp == 0) reduce_parts(part, gd, dd, nz);
