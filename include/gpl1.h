@@ -171,6 +171,42 @@ gpl1_status gpl1_solve(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype k_dty
 gpl1_status gpl1_solve_batched(gpl1_ctx* ctx, const gpl1_problem* probs, int count,
                                gpl1_dtype k_dtype, const gpl1_params* prm, gpl1_result* res);
 
+/* ---- Solve without allocating (an addition of this library; the paper has
+ * no counterpart).
+ *
+ * gpl1_solve_noalloc runs the same solver as gpl1_solve but needs no context
+ * and allocates nothing, on the device or pinned on the host.  Its workspace
+ * is one fixed array of GPL1_NOALLOC_SCRATCH_BYTES bytes built into the
+ * library, one per device.  It is for callers that must not allocate at solve
+ * time: code that runs under a device-memory budget fixed in advance, loops
+ * with a latency bound where an allocation could stall on the driver, or
+ * programs whose framework allocator owns all device memory and must not be
+ * bypassed.
+ *
+ *  - Setup: the first call on a device, made with that device current, looks
+ *    up the address of the array (which also loads the library's device code).
+ *    Make that first call before any stream capture begins, e.g. at start-up.
+ *  - Size limit: one instance needs about 12 p + 32 n bytes for F32 and BF16
+ *    (24 p + 48 n for F64), plus about 20 KB.  A problem that needs more than
+ *    GPL1_NOALLOC_SCRATCH_BYTES is rejected with GPL1_ERR_UNSUPPORTED and a
+ *    message in err, before anything is enqueued.
+ *  - Zero state: the call clears every part of the array that the kernel
+ *    accumulates into (barrier counters, gradient and K-product buffers) before
+ *    it launches, so nothing has to be zero on entry; x is cleared only when
+ *    prm->x0_is_zero is set, exactly as in gpl1_solve.
+ *  - Overlapping calls race: there is one array per device, so two calls that
+ *    overlap on the same device (from two host threads, or on two streams)
+ *    overwrite each other's workspace.  Serialise them.  Each call synchronises
+ *    cuda_stream before it returns, so consecutive calls from one thread are
+ *    safe.
+ *  - Arguments and results as in gpl1_solve; res (host) gets kernel_ms = 0
+ *    (no CUDA events are created).  cuda_stream: a cudaStream_t of the current
+ *    device (0: the legacy default stream).  err: optional host buffer of
+ *    err_len bytes that receives a message when the call fails. */
+#define GPL1_NOALLOC_SCRATCH_BYTES (4u << 20)
+gpl1_status gpl1_solve_noalloc(const gpl1_problem* prob, gpl1_dtype k_dtype, const gpl1_params* prm,
+                               gpl1_result* res, void* cuda_stream, char* err, int err_len);
+
 #ifdef __cplusplus
 }
 #endif

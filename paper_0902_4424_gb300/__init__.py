@@ -29,7 +29,7 @@ TRACE_COLS = 24
 ALGORITHMIC = (0, 3, 4, 5, 6)
 
 EXPORTS = ["gpl1_create", "gpl1_destroy", "gpl1_set_stream", "gpl1_last_error", "gpl1_params_default",
-           "gpl1_project", "gpl1_solve", "gpl1_solve_batched"]
+           "gpl1_project", "gpl1_solve", "gpl1_solve_batched", "gpl1_solve_noalloc"]
 
 
 class Gpl1Error(RuntimeError):
@@ -90,6 +90,8 @@ def lib():
                                  ctypes.POINTER(Params), ctypes.POINTER(Result)]
         L.gpl1_solve_batched.argtypes = [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(Params), ctypes.POINTER(Result)]
+        L.gpl1_solve_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, ctypes.POINTER(Params),
+                                         ctypes.POINTER(Result), ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -223,3 +225,30 @@ class Context:
         if st not in ALGORITHMIC:
             self._check(st)
         return list(res)
+
+
+NOALLOC_SCRATCH_BYTES = 4 << 20
+
+
+def solve_noalloc(K, y, rho, x=None, p=None, params: Params | None = None, f_star: float = -1.0):
+    """gpl1_solve_noalloc: one solve with the library's static scratch instead of
+    a context's workspace (no allocation inside the call).  Same arguments as
+    Context.solve; enqueues on PyTorch's current stream of K's device.
+    Returns (x, Result); raises Gpl1Error on argument, size or CUDA errors."""
+    import torch
+    code = _dtype_code(K)
+    n, ldk = K.shape
+    p = ldk if p is None else int(p)
+    prm = params_default() if params is None else params
+    if x is None:
+        x = torch.zeros(p, dtype=torch.float64 if code == F64 else torch.float32, device=K.device)
+        prm = Params.from_buffer_copy(prm)
+        prm.x0_is_zero = 1
+    pr = Context.make_problem(K, y, rho, x, p, f_star)
+    res = Result()
+    err = ctypes.create_string_buffer(256)
+    st = lib().gpl1_solve_noalloc(ctypes.byref(pr), code, ctypes.byref(prm), ctypes.byref(res), _stream_handle(),
+                                  err, len(err))
+    if st not in ALGORITHMIC:   # argument, size and CUDA errors raise; solver outcomes are in res.status
+        raise Gpl1Error(st, err.value.decode())
+    return x, res

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -428,3 +429,133 @@ gpl1_status gpl1_solve_batched(gpl1_ctx* ctx, const gpl1_problem* probs, int cou
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// gpl1_solve_noalloc: gpl1_solve with its workspace in a fixed static device
+// array instead of context memory (declaration and contract in gpl1.h).
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GPL1_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+gpl1_status noalloc_fail(char* err, int err_len, gpl1_status st, const char* msg) {
+  if (err && err_len > 0) std::snprintf(err, static_cast<size_t>(err_len), "%s", msg);
+  return st;
+}
+
+}  // namespace
+
+extern "C" gpl1_status gpl1_solve_noalloc(const gpl1_problem* prob, gpl1_dtype dt, const gpl1_params* prm,
+                                          gpl1_result* res, void* cuda_stream, char* err, int err_len) {
+  if (err && err_len > 0) err[0] = 0;
+  gpl1_ctx c;   // on the stack: argument checks and their messages only
+  if (dt != GPL1_F64 && dt != GPL1_F32 && dt != GPL1_BF16)
+    return noalloc_fail(err, err_len, GPL1_ERR_INVALID_ARG, "bad dtype");
+  if (!res) return noalloc_fail(err, err_len, GPL1_ERR_INVALID_ARG, "result is NULL");
+  gpl1_status st = check_params(&c, prm);
+  if (st == GPL1_OK) st = check_problem(&c, prob, dt, 0);
+  if (st != GPL1_OK) return noalloc_fail(err, err_len, st, c.err);
+
+  // workspace layout of a single solve: [counters][desc][result][gbuf][kbuf][pbuf]
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  int num_sms = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return noalloc_fail(err, err_len, GPL1_ERR_CUDA, cudaGetErrorString(e));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return noalloc_fail(err, err_len, GPL1_ERR_UNSUPPORTED, "device index too large");
+  const Sizes s = sizes_of(prob, dt);
+  const int as = acc_size(dt);
+  const size_t off_desc = 256;
+  const size_t off_res = align_up(off_desc + sizeof(InstDesc), 256);
+  const size_t off_g = align_up(off_res + sizeof(gpl1_result), 256);
+  const size_t off_k = align_up(off_g + 3 * s.pp * as, 256);
+  const size_t off_p = align_up(off_k + 2 * kbuf_stride(s.nn, as), 256);
+  const size_t total = align_up(off_p + 32 * static_cast<size_t>(num_sms) * 4, 256);
+  if (total > GPL1_NOALLOC_SCRATCH_BYTES) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg, "problem needs %zu bytes of scratch; the static scratch holds %u (GPL1_NOALLOC_SCRATCH_BYTES)",
+                  total, static_cast<unsigned>(GPL1_NOALLOC_SCRATCH_BYTES));
+    return noalloc_fail(err, err_len, GPL1_ERR_UNSUPPORTED, msg);
+  }
+
+  // per-device setup, once: the scratch address (this also loads the module)
+  uint8_t* ws = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* a = nullptr;
+      e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+      if (e != cudaSuccess || !a) return noalloc_fail(err, err_len, GPL1_ERR_CUDA, cudaGetErrorString(e));
+      g_noalloc_addr[dev] = a;
+    }
+    ws = static_cast<uint8_t*>(g_noalloc_addr[dev]);
+  }
+
+  CUtensorMap tmap;
+  std::memset(&tmap, 0, sizeof tmap);
+  st = encode_tmap(&c, &tmap, prob, dt);
+  if (st != GPL1_OK) return noalloc_fail(err, err_len, st, c.err);
+  struct {
+    InstDesc d;
+    gpl1_result r;
+  } host;   // staged by value (pageable copies complete before cudaMemcpyAsync returns)
+  std::memset(&host, 0, sizeof host);
+  InstDesc& d = host.d;
+  d.y = prob->y;
+  d.x = prob->x;
+  d.rho = prob->rho;
+  d.f_star = prob->f_star >= 0 ? prob->f_star : prm->f_star;
+  d.n = static_cast<int>(prob->n);
+  d.p = static_cast<int>(prob->p);
+  d.x0_zero = prm->x0_is_zero ? 1 : 0;
+  d.gbuf = ws + off_g;
+  d.kbuf = ws + off_k;
+  d.res = reinterpret_cast<gpl1_result*>(ws + off_res);
+  d.tmap = nullptr;
+  d.trace = prob->trace;
+  d.trace_cap = prob->trace ? prob->trace_cap : 0;
+  d.pbuf = ws + off_p;
+  host.r.status = GPL1_ERR_TIMEOUT;   // overwritten by the kernel
+  host.r.stop = GPL1_STOP_ERROR;
+
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  const void* fn = gpss_kernel_ptr(dt);
+  int occ = 0;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(gpss_smem_bytes(dt)));
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, gpss_smem_bytes(dt));
+  if (e == cudaSuccess && occ < 1) return noalloc_fail(err, err_len, GPL1_ERR_CUDA, "solver kernel does not fit on an SM");
+  // zero what the kernel accumulates into: counters, gbuf, kbuf, pbuf; then x0 = 0 if asked
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, off_desc, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws + off_g, 0, total - off_g, stream);
+  if (e == cudaSuccess && prm->x0_is_zero)
+    e = cudaMemsetAsync(prob->x, 0, static_cast<size_t>(prob->p) * (dt == GPL1_F64 ? 8 : 4), stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ws + off_desc, &host.d, sizeof(InstDesc), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ws + off_res, &host.r, sizeof(gpl1_result), cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return noalloc_fail(err, err_len, GPL1_ERR_CUDA, cudaGetErrorString(e));
+
+  KArgs ka;
+  ka.desc = reinterpret_cast<const InstDesc*>(ws + off_desc);
+  ka.count = 1;
+  ka.queue = reinterpret_cast<unsigned*>(ws + 0);
+  ka.bar = reinterpret_cast<unsigned*>(ws + 64);
+  ka.err = reinterpret_cast<int*>(ws + 128);
+  ka.prm = to_kernel_params(prm);
+  const long long G = std::min<long long>(static_cast<long long>(num_sms) * occ, s.units);
+  ka.group = static_cast<int>(G);
+  e = launch_gpss(dt, ka, tmap, ka.group, G > 1, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host.r, ws + off_res, sizeof(gpl1_result), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return noalloc_fail(err, err_len, GPL1_ERR_CUDA, cudaGetErrorString(e));
+  *res = host.r;
+  res->kernel_ms = 0.0;   // no events: timing is left to the caller
+  if (res->status != GPL1_OK && res->status != GPL1_ERR_NOT_CONVERGED) {
+    char msg[64];
+    std::snprintf(msg, sizeof msg, "the solve failed (status %d)", res->status);
+    return noalloc_fail(err, err_len, static_cast<gpl1_status>(res->status), msg);
+  }
+  return GPL1_OK;
+}
