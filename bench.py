@@ -174,6 +174,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------- multi-rank helpers
+def max_over_ranks(value_ms: float, world: int, device=None) -> float:
+    """The slowest rank's time: every rank passes its own, every rank gets the max."""
+    if world <= 1:
+        return float(value_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, max_total_ms: float) -> float:
+    """Solves per second of the whole job: every rank solved `steps` instances (weak scaling)."""
+    return world * steps / (max_total_ms / 1e3)
+
+
 # -------------------------------------------------------------- GPU path
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -233,11 +250,8 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
-    value = world * args.steps / (total_ms_max / 1e3)
+    total_ms_max = max_over_ranks(total_ms, world, dev)
+    value = whole_job_rate(world, args.steps, total_ms_max)
 
     # ---- check the objective actually reached (FP64 on the host, untimed)
     import oracle
@@ -262,10 +276,7 @@ def run_ours(args, rank, world, local_rank):
         b.record(stream)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    t = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps / (float(t.item()) / 1e3)
+    e2e_value = whole_job_rate(world, args.steps, max_over_ranks(sum(e2e_ms), world, dev))
 
     if rank != 0:
         return
@@ -277,7 +288,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = algo_bytes / (kms / 1e3) / 1e9
     peak, peak_kind = peaks()
     traffic = None
-    tr_file = os.path.join(ROOT, "profiles", "gpss_kernel_traffic.json")
+    tr_file = os.path.join(ROOT, "profiles", "gpss_kernel_c1_f32_traffic.txt")   # JSON text
     if os.path.exists(tr_file):
         with open(tr_file) as fh:
             tr = json.load(fh)
