@@ -191,6 +191,77 @@ def whole_job_rate(world: int, steps: int, max_total_ms: float) -> float:
     return world * steps / (max_total_ms / 1e3)
 
 
+# ------------------------------------------------- batched ragged form (c3a)
+def run_batched(count, steps, dev):
+    """Solves/s of `count` instances of the ragged recipe (n in [128, 2048], p = 4n,
+    BF16 K, +-1 signals): one persistent gpl1_solve_batched launch per step, and the
+    same instances solved one after another with gpl1_solve (the plain form).  Each
+    instance stops at relative gap 1e-6 against the oracle's optimum of that instance
+    (tests/golden/c3a_fstar.json, written by tests/golden/make_golden.py)."""
+    import torch
+
+    import oracle
+    import paper_0902_4424_gb300 as pkg
+    import workloads as W
+    sizes = W.ragged_sizes(512)[:count]
+    probs = [W.ragged_instance(i, n) for i, n in enumerate(sizes)]
+    with open(os.path.join(ROOT, "tests", "golden", "c3a_fstar.json")) as fh:
+        fstars = json.load(fh)["f_star"][:count]
+    keep, descs = [], []
+    for pr, fs in zip(probs, fstars):
+        K = torch.from_numpy(pr.K.view(np.int16)).to(dev)
+        y = torch.from_numpy(pr.y).to(dev)
+        x = torch.zeros(pr.p, dtype=torch.float32, device=dev)
+        keep.append((K, y, x))
+        descs.append(pkg.Context.make_problem(K, y, pr.rho, x, pr.p, fs))
+    ctx = pkg.Context(dev.index or 0)
+    # the kernel decides on its own (float) estimate of f: stop at half the target
+    # so that the gap the oracle verifies on the returned x stays within 1e-6
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=0.5 * TOL, x0_is_zero=1, max_iter=20000)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        ctx.solve_batched(descs, pkg.BF16, prm)
+    torch.cuda.synchronize()
+    ms, kms, res = [], [], None
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = ctx.solve_batched(descs, pkg.BF16, prm)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        kms.append(res[0].kernel_ms)
+    ok = sum(r.status == 0 for r in res)
+    iters = [r.iters for r in res]
+    algo = sum(it * 2.0 * pr.n * pr.p * 2 for it, pr in zip(iters, probs))
+    # the plain form: the same instances one after another, each its own cooperative launch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plain_ok = 0
+    for (K, y, x), pr, fs in zip(keep, probs, fstars):
+        _, r = ctx.solve(K, y, pr.rho, x=x, p=pr.p, params=prm, f_star=fs)
+        plain_ok += r.status == 0
+    b.record(stream)
+    b.synchronize()
+    plain_ms = a.elapsed_time(b)
+    # untimed: the oracle's optimum on a few instances, against the batched x
+    ctx.solve_batched(descs, pkg.BF16, prm)
+    torch.cuda.synchronize()
+    gaps = [(oracle.objective(probs[q], keep[q][2].double().cpu().numpy()) - fstars[q]) / max(fstars[q], 1e-300)
+            for q in range(count)]
+    peak, _ = peaks()
+    mean_ms = statistics.mean(ms)
+    out = {"workload": f"c3a_ragged{count}_bf16", "instances": count, "solves_per_s": count / (mean_ms / 1e3),
+           "ms_per_batch": mean_ms, "ok": ok, "iters_mean": statistics.mean(iters), "iters_max": max(iters),
+           "plain_solves_per_s": count / (plain_ms / 1e3), "plain_ok": plain_ok,
+           "speedup_vs_plain": plain_ms / mean_ms, "stop": f"kernel stop rel_gap<={0.5 * TOL:g} vs oracle f* per instance",
+           "verified_max_rel_gap": max(gaps) if gaps else None, "verified_instances": len(gaps),
+           "hbm_gbs": algo / (statistics.mean(kms) / 1e3) / 1e9}
+    out["roofline_frac"] = out["hbm_gbs"] / peak
+    ctx.close()
+    return out
+
+
 # -------------------------------------------------------------- GPU path
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -324,6 +395,8 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
+    if args.batched_sample > 0:
+        line["batched"] = run_batched(args.batched_sample, 3, dev)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -348,6 +421,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-sample", type=int, default=64,
+                    help="also time this many ragged instances batched vs plain (0: skip)")
+    ap.add_argument("--workload", choices=["c1", "c3a"], default="c1",
+                    help="c3a: only the batched ragged form, all 512 instances")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -362,6 +439,16 @@ def main():
             dist.init_process_group("gloo")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "c3a":
+        import torch
+        torch.cuda.set_device(local_rank)
+        out = run_batched(512, max(1, args.steps // 20), torch.device("cuda", local_rank))
+        if rank == 0:
+            print(json.dumps({"metric": load_baseline_metric(), "value": out["solves_per_s"], "unit": "solves/s",
+                              "n_gpus": world, "steps": max(1, args.steps // 20), "warmup": 2,
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                              "data": "synthetic", "config": {"workload": out["workload"]}, "batched": out}),
+                  flush=True)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

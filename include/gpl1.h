@@ -124,13 +124,16 @@ typedef struct {
                      projection threshold, then the nanoseconds from the start of
                      iteration k to the end of: pass A, its barrier, the projection
                      phase, pass B, its barrier, the phase-P reductions, Alg. SS, the
-                     threshold search; then the number of threshold-search steps and
-                     seven clock stamps inside the search),
-                     written for k < trace_cap; NULL for none                        */
+                     threshold search; then the number of threshold-search steps, six
+                     clock stamps inside the search and the number of candidates it
+                     kept; then, as raw globaltimer values (the bits of the double
+                     slots), the earliest and latest end of pass A and of pass B over
+                     all CTAs), written for k < trace_cap (the rows must start zeroed);
+                     NULL for none                                                   */
   long long trace_cap;
 } gpl1_problem;
 
-#define GPL1_TRACE_COLS 24
+#define GPL1_TRACE_COLS 28
 
 /* Create a context on CUDA device `device` that enqueues on `cuda_stream`
  * (a cudaStream_t; 0 means the legacy default stream).  *out receives the

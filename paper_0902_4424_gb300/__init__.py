@@ -24,7 +24,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NOT_CONVERGED", 4: "LINESEAR
 STOP = {0: "rel_gap", 1: "stationary", 2: "fw", 3: "max_iter", 4: "error"}
 STOP_ON_REL_GAP, STOP_ON_FW = 1, 2
 DEBUG_UNREACHABLE_BARRIER = 1
-TRACE_COLS = 24
+TRACE_COLS = 28
 # statuses that describe how a solve ended (reported in Result.status, not raised)
 ALGORITHMIC = (0, 3, 4, 5, 6)
 

@@ -98,6 +98,9 @@ constexpr uint64_t kInflightNs = 2000000000ull;
 // requested stop is below this many times the tolerance (FP32 sums of K x
 // carry about 1e-7 relative noise into f).
 constexpr double kAccGapFactor = 100.0;
+// ... and, whatever the stop rule, once an iteration decreases f by less than
+// this fraction of f.
+constexpr double kAccDecrease = 1e-5;
 
 // SolveParams.debug bit: the group barrier waits for one arrival more than the
 // group has, so every wait runs out.  Exercises the bounded-wait error path.
@@ -910,6 +913,16 @@ struct Consumer {
     }
   }
 
+  // Columns c, c+1 of row k: the earliest and latest of every CTA's stamp t
+  // (raw globaltimer bits in the double slots; the row starts zeroed).
+  __device__ void trace_spread(int k, int c, unsigned long long t) {
+    if (!D.trace || k >= D.trace_cap) return;
+    unsigned long long* r = reinterpret_cast<unsigned long long*>(D.trace + static_cast<long long>(k) * GPL1_TRACE_COLS);
+    atomicCAS(r + c, 0ull, ~0ull);   // the first CTA turns the "min" slot into +inf
+    atomicMin(r + c, t);
+    atomicMax(r + c + 1, t);
+  }
+
   __device__ void trace_row(int k, double fk, double lam, double kb2) {
     Uni& u = sm.uni;
     if (D.trace && k < D.trace_cap && cta == 0) {
@@ -925,7 +938,8 @@ struct Consumer {
       for (int q = 0; q < 5; ++q) t[8 + q] = static_cast<double>(u.ts[q] - u.ts[5]);
       for (int q = 6; q < 9; ++q) t[7 + q] = static_cast<double>(u.ts[q] - u.ts[5]);
       t[16] = u.psteps;
-      for (int q = 1; q < 8; ++q) t[16 + q] = static_cast<double>(u.tt[q] - u.tt[0]);
+      for (int q = 1; q < 7; ++q) t[16 + q] = static_cast<double>(u.tt[q] - u.tt[0]);
+      t[23] = static_cast<double>(u.tt[7]);   // candidates kept by the threshold search
     }
   }
 
@@ -990,6 +1004,7 @@ struct Consumer {
     if ((P.stop_rule & GPL1_STOP_ON_REL_GAP) && D.f_star >= 0.0 &&
         fnext - D.f_star <= kAccGapFactor * P.tol * u.gap_den)
       u.acc_kx = 1;
+    if (fk - fnext <= kAccDecrease * fk) u.acc_kx = 1;   // progress near the FP32 resolution of f
     if ((P.stop_rule & GPL1_STOP_ON_REL_GAP) && D.f_star >= 0.0 && fnext - D.f_star <= P.tol * u.gap_den) {
       u.stop = GPL1_STOP_REL_GAP;
       u.done = 1;
@@ -1098,7 +1113,10 @@ struct Consumer {
         if (!kF64 && u.kmode[(k + 1) & 1]) pass_a<true>(kp_of((k + 1) & 1), kx_of((k + 1) & 1), lp, gk);
         else pass_a<false>(kp_of((k + 1) & 1), kx_of((k + 1) & 1), lp, gk);
       }
-      if (tid == 0 && D.trace) u.ts[0] = globaltimer();
+      if (tid == 0 && D.trace) {
+        u.ts[0] = globaltimer();
+        trace_spread(k, 24, u.ts[0]);
+      }
       if (!group_sync()) break;
       if (tid == 0 && D.trace) u.ts[1] = globaltimer();
 
@@ -1196,7 +1214,10 @@ struct Consumer {
       // ---------------- pass B: [K d_k, K x_k], g^T d, ||d||^2
       if (!kF64 && u.kmode[k & 1]) pass_b<true>(gk, Dir(u), kp_of(k & 1), kx_of(k & 1), part);
       else pass_b<false>(gk, Dir(u), kp_of(k & 1), kx_of(k & 1), part);
-      if (tid == 0 && D.trace) u.ts[3] = globaltimer();
+      if (tid == 0 && D.trace) {
+        u.ts[3] = globaltimer();
+        trace_spread(k, 26, u.ts[3]);
+      }
       if (!group_sync()) break;
       if (tid == 0 && D.trace) u.ts[4] = globaltimer();
 

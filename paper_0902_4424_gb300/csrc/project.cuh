@@ -539,6 +539,10 @@ __device__ __noinline__ TauResult block_l1_tau_fixed_point(const Acc& acc, doubl
   consumer_sync();
   const int ncand = sc.flags[2];
   const bool compact = ncand <= kCandCap;
+  if (lead) {
+    sc.tt[5] = clock64();
+    sc.tt[7] = ncand;
+  }
   consumer_sync();
   for (int step = 0; step < kFixedPointCap; ++step) {
     const TauPair tp{sc.tp[2], sc.tp[3]};
@@ -610,7 +614,10 @@ __device__ __noinline__ TauResult block_l1_tau_fixed_point(const Acc& acc, doubl
         tau = sc.dtau;
       }
       const TauResult r{tau, 0.0, 0, sc.tp[2], sc.tp[3]};
-      if (lead) sc.flags[2] = sc.flags[1];   // report the step count
+      if (lead) {
+        sc.flags[2] = sc.flags[1];   // report the step count
+        sc.tt[6] = clock64();
+      }
       consumer_sync();
       return r;
     }

@@ -5,6 +5,7 @@ inputs of workloads/ to its precision floor (Frank-Wolfe certificate 1e-13 or
 no decrease of f for 30 iterations).  Nothing here touches the CUDA path.
 
     python tests/golden/make_golden.py [c0 c1 c2 ...]
+    python tests/golden/make_golden.py c3a      # the ragged batch: c3a_fstar.json
 """
 import json
 import os
@@ -40,5 +41,26 @@ def main(names):
             json.dump(gold, fh, indent=1, sort_keys=True)
 
 
+def main_c3a(count=512):
+    """tests/golden/c3a_fstar.json: f* of the ragged batch's instances (the
+    oracle's floor solve: iterate until the FP64 line search cannot decrease f)."""
+    out = os.path.join(os.path.dirname(OUT), "c3a_fstar.json")
+    t = time.time()
+    sizes = W.ragged_sizes(count)
+    fs = []
+    for i, n in enumerate(sizes):
+        prob = W.ragged_instance(i, n)
+        fs.append(oracle.floor_solve(prob)[1].f)
+        if i % 64 == 63:
+            print(i + 1, f"{time.time() - t:.0f}s", flush=True)
+    with open(out, "w") as fh:
+        json.dump({"workload": f"c3a_ragged{count}_bf16", "n": sizes, "f_star": fs,
+                   "solver": "oracle.floor_solve"}, fh, indent=0)
+
+
 if __name__ == "__main__":
-    main(sys.argv[1:] or list(CONFIGS))
+    args = sys.argv[1:]
+    if args == ["c3a"]:
+        main_c3a()
+    else:
+        main(args or list(CONFIGS))

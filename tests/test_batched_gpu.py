@@ -1,6 +1,9 @@
 """gpl1_solve_batched: many independent instances of uneven n, p in one
 persistent launch, each checked against the FP64 oracle at the same bars as
 single solves (relative objective gap <= 1e-6, feasibility)."""
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -55,9 +58,10 @@ def test_ragged_batch_config3_shapes(gpu_ctx):
     """Instances drawn like the 512-instance ragged batch (n in [128, 2048],
     p = 4n, BF16 K, +-1 signals with n/20 non-zeros): the first 16 of them,
     each against the oracle's optimum."""
-    sizes = W.ragged_sizes(16)
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c3a_fstar.json")))
+    sizes = gold["n"][:16]
     probs = [W.ragged_instance(i, n) for i, n in enumerate(sizes)]
-    refs = [oracle.floor_solve(pr)[1].f for pr in probs]
+    refs = gold["f_star"][:16]
     xs, res = run_batch(gpu_ctx, probs, W.DT_BF16, refs)
     for pr, x, r, fs in zip(probs, xs, res, refs):
         gap = (oracle.objective(pr, x) - fs) / fs

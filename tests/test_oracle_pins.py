@@ -311,3 +311,14 @@ def test_golden_fstar_values_match_oracle_small():
     prob = W.config0()
     x, res, _ = oracle.reference_solve(prob)
     assert abs(res.f - gold["c0"]["f_star"]) <= 1e-12 * res.f
+
+
+def test_golden_c3a_fstar_match_oracle():
+    """The stored optima of the ragged batch are the oracle's: recompute the two smallest."""
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c3a_fstar.json")))
+    assert gold["n"] == W.ragged_sizes(len(gold["n"]))
+    order = np.argsort(gold["n"])[:2]
+    for i in order:
+        prob = W.ragged_instance(int(i), gold["n"][i])
+        f = oracle.floor_solve(prob)[1].f
+        assert abs(f - gold["f_star"][i]) <= 1e-12 * gold["f_star"][i]
