@@ -174,6 +174,21 @@ gpl1_status gpl1_solve(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype k_dty
 gpl1_status gpl1_solve_batched(gpl1_ctx* ctx, const gpl1_problem* probs, int count,
                                gpl1_dtype k_dtype, const gpl1_params* prm, gpl1_result* res);
 
+/* Tensor-core product used by the shared-K form of the method (many
+ * right-hand sides on one K turn K^T r and K d into matrix products):
+ *   out[n * ldo + m] = scale * sum_{k < Kd} A[m * lda + (k mod Ka)] * B[n * ldb + k]
+ * for 0 <= m < M, 0 <= n < N.  A (M x Ka) and B (N x Kd) are bfloat16 (raw
+ * 16-bit patterns), row-major with K contiguous; the products accumulate in
+ * FP32 on the tcgen05 tensor cores.  Ka and Kd are positive multiples of 64
+ * (a B longer than A along K multiplies A repeatedly: B = [b_hi | b_mid | b_lo]
+ * against [A A A] is how an FP32 vector operand is carried in BF16 terms).
+ * A, B and their row strides must be 16-byte aligned; out is FP32 (device),
+ * written transposed (column n of the product is contiguous).  The call
+ * synchronises the context stream. */
+gpl1_status gpl1_gemm_bf16(gpl1_ctx* ctx, const void* A, long long M, long long Ka, long long lda,
+                           const void* B, long long N, long long Kd, long long ldb, float* out,
+                           long long ldo, float scale);
+
 /* ---- Solve without allocating (an addition of this library; the paper has
  * no counterpart).
  *

@@ -29,7 +29,7 @@ TRACE_COLS = 28
 ALGORITHMIC = (0, 3, 4, 5, 6)
 
 EXPORTS = ["gpl1_create", "gpl1_destroy", "gpl1_set_stream", "gpl1_last_error", "gpl1_params_default",
-           "gpl1_project", "gpl1_solve", "gpl1_solve_batched", "gpl1_solve_noalloc"]
+           "gpl1_project", "gpl1_solve", "gpl1_solve_batched", "gpl1_solve_noalloc", "gpl1_gemm_bf16"]
 
 
 class Gpl1Error(RuntimeError):
@@ -90,6 +90,9 @@ def lib():
                                  ctypes.POINTER(Params), ctypes.POINTER(Result)]
         L.gpl1_solve_batched.argtypes = [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(Params), ctypes.POINTER(Result)]
+        L.gpl1_gemm_bf16.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
+                                     ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
+                                     ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_float]
         L.gpl1_solve_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, ctypes.POINTER(Params),
                                          ctypes.POINTER(Result), ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]
         _lib = L
@@ -179,6 +182,22 @@ class Context:
         del keep
         self._check(st)
         return out.view_as(v)
+
+    # --------------------------------------------------------------- gemm
+    def gemm_bf16(self, A, B, Kd=None, out=None, scale=1.0):
+        """gpl1_gemm_bf16: out (N, M) FP32 with out[n, m] = scale * sum_k A[m, k % Ka] B[n, k].
+        A (M, Ka) and B (N, Kd) are bfloat16 (or int16 bit patterns), K contiguous."""
+        import torch
+        M, Ka = A.shape
+        N, Kb = B.shape
+        Kd = Kb if Kd is None else int(Kd)
+        out = torch.empty(N, M, dtype=torch.float32, device=A.device) if out is None else out
+        self._bind_stream()
+        st = lib().gpl1_gemm_bf16(self._h, ctypes.c_void_p(A.data_ptr()), M, Ka, A.stride(0),
+                                  ctypes.c_void_p(B.data_ptr()), N, Kd, B.stride(0),
+                                  ctypes.c_void_p(out.data_ptr()), out.stride(0), float(scale))
+        self._check(st)
+        return out
 
     # -------------------------------------------------------------- solve
     @staticmethod

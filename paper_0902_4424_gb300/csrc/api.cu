@@ -559,3 +559,44 @@ extern "C" gpl1_status gpl1_solve_noalloc(const gpl1_problem* prob, gpl1_dtype d
   }
   return GPL1_OK;
 }
+
+// ---------------------------------------------------------------------------
+// gpl1_gemm_bf16: the tensor-core product of the shared-K form (gemm_tc.cu).
+
+extern "C" gpl1_status gpl1_gemm_bf16(gpl1_ctx* ctx, const void* A, long long M, long long Ka, long long lda,
+                                      const void* B, long long N, long long Kd, long long ldb, float* out,
+                                      long long ldo, float scale) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  if (!A || !B || !out) return fail(ctx, GPL1_ERR_INVALID_ARG, "NULL pointer");
+  if (M < 1 || N < 1 || Ka < 64 || Kd < 64 || Ka % 64 || Kd % 64)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "need M, N >= 1 and Ka, Kd positive multiples of 64");
+  if (lda < Ka || ldb < Kd || ldo < M) return fail(ctx, GPL1_ERR_INVALID_ARG, "need lda >= Ka, ldb >= Kd, ldo >= M");
+  if ((lda * 2) % 16 || (ldb * 2) % 16 || reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(B) % 16)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "A, B and their row strides must be 16-byte aligned");
+  if (M > (1LL << 30) || N > (1LL << 30) || Kd > (1LL << 30))
+    return fail(ctx, GPL1_ERR_UNSUPPORTED, "dimension too large");
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (!ctx->encode) {   // the driver's tensor-map encoder (as for the solver)
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    GPL1_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q),
+              "cudaGetDriverEntryPointByVersion");
+    if (q != cudaDriverEntryPointSuccess || !fn) return fail(ctx, GPL1_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    ctx->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  gpl1_status st = ensure_ws(ctx, 256);
+  if (st) return st;
+  int* err = static_cast<int*>(ctx->ws);
+  GPL1_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream), "cudaMemsetAsync");
+  const int bn = N > 128 ? 256 : 128;
+  const int e = launch_gemm_bf16(ctx->encode, A, static_cast<int>(M), static_cast<int>(Ka), lda, B,
+                                 static_cast<int>(N), static_cast<int>(Kd), ldb, out, ldo, scale, err,
+                                 10LL * 1000 * 1000 * 1000, bn, ctx->stream);
+  if (e == -1) return fail(ctx, GPL1_ERR_CUDA, "tensor map encoding failed");
+  if (e != 0) return cuda_fail(ctx, static_cast<cudaError_t>(e), "gemm launch");
+  int herr = 0;
+  GPL1_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "cudaMemcpyAsync");
+  GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "gemm");
+  if (herr) return fail(ctx, static_cast<gpl1_status>(herr), "a bounded wait in the GEMM ran out");
+  return GPL1_OK;
+}

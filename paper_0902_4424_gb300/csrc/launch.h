@@ -4,6 +4,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cudaTypedefs.h>
+
 #include "gpss.cuh"
 
 namespace gpl1 {
@@ -20,5 +22,13 @@ int gpss_vmax(int dtype);
 cudaError_t launch_project(int dtype, const void* v, void* out, long long p, long long batch,
                            long long stride, const double* rho, double* tau, cudaStream_t stream);
 long long project_max_p(int dtype);
+
+// BF16 tensor-core GEMM (gemm_tc.cu): out[n * ldo + m] = scale * sum_k A[m][k % Ka] B[n][k],
+// A M x Ka (row stride lda), B N x Kd (row stride ldb), Kd a multiple of 64, Ka of 64.
+// bn: 128 or 256 (tile width along N).  Returns a cudaError_t, or -1 if a tensor map
+// could not be encoded.
+int launch_gemm_bf16(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* A, int M, int Ka, long long lda,
+                     const void* B, int N, int Kd, long long ldb, float* out, long long ldo, float scale, int* err,
+                     long long timeout_ns, int bn, cudaStream_t stream);
 
 }  // namespace gpl1

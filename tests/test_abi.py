@@ -17,7 +17,7 @@ HEADER = os.path.join(ROOT, "include", "gpl1.h")
 def declared_functions():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(gpl1_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(gpl1_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_library_loads_and_exports_every_declared_symbol():
