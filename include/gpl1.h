@@ -189,6 +189,22 @@ gpl1_status gpl1_gemm_bf16(gpl1_ctx* ctx, const void* A, long long M, long long 
                            const void* B, long long N, long long Kd, long long ldb, float* out,
                            long long ldo, float scale);
 
+/* Solve nrhs instances of eq. 2 that share one K (GPL1_BF16, n x p, row
+ * stride ldk) and differ in y and rho, with Alg. GP + SS per instance: the
+ * gradients 2 K^T r and the products K d, K x of all instances are formed as
+ * tensor-core matrix products (gpl1_gemm_bf16, FP32 vectors carried as three
+ * BF16 terms), the steplength, projection and line search per instance.
+ *   Y: device, nrhs rows of n floats (row stride ldy); X: device, nrhs rows of
+ *   p floats (row stride ldx), the solutions on exit (x0 = 0: prm->x0_is_zero
+ *   must be set).  rho, f_star: host arrays of nrhs doubles (f_star may be
+ *   NULL; otherwise it enables GPL1_STOP_ON_REL_GAP per instance).  res: host
+ *   array of nrhs results (kernel_ms = the whole solve).  n and p must be
+ *   multiples of 64, p <= 16800.  The call synchronises the context stream. */
+gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
+                                const float* Y, long long ldy, const double* rho, const double* f_star,
+                                float* X, long long ldx, int nrhs, const gpl1_params* prm,
+                                gpl1_result* res);
+
 /* ---- Solve without allocating (an addition of this library; the paper has
  * no counterpart).
  *

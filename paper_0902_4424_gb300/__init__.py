@@ -29,7 +29,8 @@ TRACE_COLS = 28
 ALGORITHMIC = (0, 3, 4, 5, 6)
 
 EXPORTS = ["gpl1_create", "gpl1_destroy", "gpl1_set_stream", "gpl1_last_error", "gpl1_params_default",
-           "gpl1_project", "gpl1_solve", "gpl1_solve_batched", "gpl1_solve_noalloc", "gpl1_gemm_bf16"]
+           "gpl1_project", "gpl1_solve", "gpl1_solve_batched", "gpl1_solve_noalloc", "gpl1_gemm_bf16",
+           "gpl1_solve_shared_k"]
 
 
 class Gpl1Error(RuntimeError):
@@ -93,6 +94,10 @@ def lib():
         L.gpl1_gemm_bf16.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_float]
+        L.gpl1_solve_shared_k.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
+                                          ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
+                                          ctypes.POINTER(Params), ctypes.POINTER(Result)]
         L.gpl1_solve_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, ctypes.POINTER(Params),
                                          ctypes.POINTER(Result), ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]
         _lib = L
@@ -232,6 +237,28 @@ class Context:
         if st not in ALGORITHMIC:   # argument / CUDA errors raise; solver outcomes are in res.status
             self._check(st)
         return x, res
+
+    def solve_shared_k(self, K, Y, rho, p=None, f_star=None, params: Params | None = None, X=None):
+        """gpl1_solve_shared_k: instances sharing the BF16 K (n, ldk) with right-hand sides
+        Y (nrhs, n) float32 and radii rho (nrhs); returns (X (nrhs, p) float32, [Result])."""
+        import torch
+        n, ldk = K.shape
+        nrhs = Y.shape[0]
+        p = ldk if p is None else int(p)
+        X = torch.empty(nrhs, p, dtype=torch.float32, device=K.device) if X is None else X
+        prm = Params.from_buffer_copy(params_default() if params is None else params)
+        prm.x0_is_zero = 1
+        rho_h = (ctypes.c_double * nrhs)(*[float(r) for r in rho])
+        fs_h = None if f_star is None else (ctypes.c_double * nrhs)(*[float(f) for f in f_star])
+        res = (Result * nrhs)()
+        self._bind_stream()
+        st = lib().gpl1_solve_shared_k(self._h, ctypes.c_void_p(K.data_ptr()), n, p, ldk,
+                                       ctypes.c_void_p(Y.data_ptr()), Y.stride(0), ctypes.cast(rho_h, ctypes.c_void_p),
+                                       ctypes.cast(fs_h, ctypes.c_void_p) if fs_h is not None else None,
+                                       ctypes.c_void_p(X.data_ptr()), X.stride(0), nrhs, ctypes.byref(prm), res)
+        if st not in ALGORITHMIC:
+            self._check(st)
+        return X, list(res)
 
     def solve_batched(self, problems: Sequence[Problem], dtype: int, params: Params | None = None):
         """Solve independent instances in one persistent launch (gpl1_solve_batched); returns results."""

@@ -16,7 +16,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libgpl1.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["api.cu", "project.cu", "gpss_f64.cu", "gpss_f32.cu", "gpss_bf16.cu", "gemm_tc.cu"]
+SOURCES = ["api.cu", "project.cu", "gpss_f64.cu", "gpss_f32.cu", "gpss_bf16.cu", "gemm_tc.cu", "shared_k.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
@@ -33,7 +33,7 @@ def _fingerprint() -> str:
             with open(os.path.join(d, name), "rb") as fh:
                 h.update(name.encode())
                 h.update(fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + FLAGS + SOURCES).encode())
     return h.hexdigest()
 
 
@@ -61,7 +61,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
+    r = subprocess.run([nvcc] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs,
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

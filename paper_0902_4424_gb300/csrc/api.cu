@@ -600,3 +600,118 @@ extern "C" gpl1_status gpl1_gemm_bf16(gpl1_ctx* ctx, const void* A, long long M,
   if (herr) return fail(ctx, static_cast<gpl1_status>(herr), "a bounded wait in the GEMM ran out");
   return GPL1_OK;
 }
+
+// ---------------------------------------------------------------------------
+// gpl1_solve_shared_k: nrhs instances sharing one BF16 K (shared_k.cu).
+
+extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
+                                           const float* Y, long long ldy, const double* rho, const double* f_star,
+                                           float* X, long long ldx, int nrhs, const gpl1_params* prm,
+                                           gpl1_result* res) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  if (!K || !Y || !rho || !X || !res || nrhs < 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "NULL pointer or nrhs < 1");
+  gpl1_status st = check_params(ctx, prm);
+  if (st) return st;
+  if (n < 64 || p < 64 || n % 64 || p % 64)
+    return fail(ctx, GPL1_ERR_UNSUPPORTED, "the shared-K form needs n and p to be multiples of 64");
+  if (p > static_cast<long long>(35) * kConsumers) return fail(ctx, GPL1_ERR_UNSUPPORTED, "p exceeds %d", 35 * kConsumers);
+  if (ldk < p || (ldk * 2) % 16 || reinterpret_cast<uintptr_t>(K) % 16)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "K rows must be 16-byte aligned, ldk >= p");
+  if (ldy < n || ldx < p) return fail(ctx, GPL1_ERR_INVALID_ARG, "need ldy >= n and ldx >= p");
+  for (int b = 0; b < nrhs; ++b)
+    if (!(rho[b] > 0) || !std::isfinite(rho[b])) return fail(ctx, GPL1_ERR_INVALID_ARG, "rho[%d] must be > 0", b);
+  if (!prm->x0_is_zero) return fail(ctx, GPL1_ERR_UNSUPPORTED, "the shared-K form starts from x0 = 0");
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (!ctx->encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    GPL1_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q),
+              "cudaGetDriverEntryPointByVersion");
+    if (q != cudaDriverEntryPointSuccess || !fn) return fail(ctx, GPL1_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    ctx->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  // workspace
+  const size_t N = static_cast<size_t>(nrhs), nn = static_cast<size_t>(n), pp = static_cast<size_t>(p);
+  size_t off = 256;   // [0] done count, [64] gemm error flag
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_kt = take(pp * nn * 2), o_g0 = take(N * pp * 4), o_g1 = take(N * pp * 4), o_d = take(N * pp * 4);
+  const size_t o_dx = take(2 * N * 3 * pp * 2), o_kdx = take(2 * N * nn * 4), o_rs = take(N * 3 * nn * 2);
+  const size_t o_st = take(N * mr_state_bytes()), o_res = take(N * sizeof(gpl1_result));
+  const size_t o_rho = take(N * 8), o_fs = take(N * 8);
+  st = ensure_ws(ctx, off);
+  if (st) return st;
+  uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
+  int* done_count = reinterpret_cast<int*>(ws);
+  int* gerr = reinterpret_cast<int*>(ws + 64);
+  uint16_t* Kt = reinterpret_cast<uint16_t*>(ws + o_kt);
+  float* G[2] = {reinterpret_cast<float*>(ws + o_g0), reinterpret_cast<float*>(ws + o_g1)};
+  float* D = reinterpret_cast<float*>(ws + o_d);
+  uint16_t* DXs = reinterpret_cast<uint16_t*>(ws + o_dx);
+  float* KDX = reinterpret_cast<float*>(ws + o_kdx);
+  uint16_t* Rs = reinterpret_cast<uint16_t*>(ws + o_rs);
+  void* states = ws + o_st;
+  gpl1_result* rdev = reinterpret_cast<gpl1_result*>(ws + o_res);
+  double* rho_d = reinterpret_cast<double*>(ws + o_rho);
+  double* fs_d = reinterpret_cast<double*>(ws + o_fs);
+  cudaStream_t s = ctx->stream;
+  GPL1_CUDA(cudaMemsetAsync(ws, 0, 256, s), "cudaMemsetAsync");
+  GPL1_CUDA(cudaMemsetAsync(G[1], 0, N * pp * 4, s), "cudaMemsetAsync");
+  GPL1_CUDA(cudaMemcpyAsync(rho_d, rho, N * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(rho)");
+  if (f_star) GPL1_CUDA(cudaMemcpyAsync(fs_d, f_star, N * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(f*)");
+  const SolveParams sp = to_kernel_params(prm);
+  if (!ctx->ev[0]) {
+    GPL1_CUDA(cudaEventCreate(&ctx->ev[0]), "cudaEventCreate");
+    GPL1_CUDA(cudaEventCreate(&ctx->ev[1]), "cudaEventCreate");
+  }
+  GPL1_CUDA(cudaEventRecord(ctx->ev[0], s), "cudaEventRecord");
+  GPL1_CUDA(launch_transpose_bf16(K, ldk, Kt, static_cast<int>(n), static_cast<int>(p), s), "transpose");
+  GPL1_CUDA(launch_mr_init(Y, ldy, X, ldx, Rs, static_cast<int>(n), static_cast<int>(p), rho_d,
+                           f_star ? fs_d : nullptr, states, sp, nrhs, s),
+            "init");
+  const long long tmo = prm->timeout_ns;
+  auto bn_for = [&](long long M, long long Nc) {
+    return ((M + 127) / 128) * ((Nc + 255) / 256) < ctx->num_sms ? 128 : 256;
+  };
+  int iters_run = 0;
+  for (int k = 0; k < prm->max_iter; ++k) {
+    float* Gc = G[k & 1];
+    float* Gp = G[(k + 1) & 1];
+    int e = launch_gemm_bf16(ctx->encode, Kt, static_cast<int>(p), static_cast<int>(n), n, Rs, nrhs,
+                             static_cast<int>(3 * n), 3 * n, Gc, p, 2.f, gerr, tmo, bn_for(p, nrhs), s);
+    if (e) return e == -1 ? fail(ctx, GPL1_ERR_CUDA, "tensor map") : cuda_fail(ctx, static_cast<cudaError_t>(e), "gemm 1");
+    GPL1_CUDA(launch_mr_phase_p(Gc, Gp, X, ldx, D, DXs, static_cast<int>(p), nrhs, k, states, sp, s), "phase P");
+    e = launch_gemm_bf16(ctx->encode, K, static_cast<int>(n), static_cast<int>(p), ldk, DXs, 2 * nrhs,
+                         static_cast<int>(3 * p), 3 * p, KDX, n, 1.f, gerr, tmo, bn_for(n, 2LL * nrhs), s);
+    if (e) return e == -1 ? fail(ctx, GPL1_ERR_CUDA, "tensor map") : cuda_fail(ctx, static_cast<cudaError_t>(e), "gemm 2");
+    GPL1_CUDA(launch_mr_phase_l(KDX, Kt, Y, ldy, X, ldx, D, Rs, static_cast<int>(n), static_cast<int>(p), nrhs, k,
+                                states, sp, rdev, done_count, s),
+              "phase L");
+    iters_run = k + 1;
+    if ((k & 3) == 3 || k + 1 == prm->max_iter) {
+      int hd[2] = {0, 0};
+      GPL1_CUDA(cudaMemcpyAsync(hd, ws, 2 * sizeof(int), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+      GPL1_CUDA(cudaStreamSynchronize(s), "shared-K iteration");
+      if (hd[0] >= nrhs) break;
+      int ge = 0;
+      GPL1_CUDA(cudaMemcpy(&ge, gerr, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy");
+      if (ge) return fail(ctx, static_cast<gpl1_status>(ge), "a bounded wait in a GEMM ran out");
+    }
+  }
+  (void)iters_run;
+  GPL1_CUDA(cudaEventRecord(ctx->ev[1], s), "cudaEventRecord");
+  GPL1_CUDA(cudaMemcpyAsync(res, rdev, N * sizeof(gpl1_result), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(res)");
+  GPL1_CUDA(cudaStreamSynchronize(s), "shared-K solve");
+  float ms = 0.f;
+  GPL1_CUDA(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]), "cudaEventElapsedTime");
+  int worst = GPL1_OK;
+  for (int b = 0; b < nrhs; ++b) {
+    res[b].kernel_ms = ms;
+    if (res[b].status != GPL1_OK && res[b].status != GPL1_ERR_NOT_CONVERGED) worst = res[b].status;
+  }
+  if (worst != GPL1_OK) return fail(ctx, static_cast<gpl1_status>(worst), "an instance failed (status %d)", worst);
+  return GPL1_OK;
+}

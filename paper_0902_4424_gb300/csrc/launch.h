@@ -32,3 +32,19 @@ int launch_gemm_bf16(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* A, int M
                      long long timeout_ns, int bn, cudaStream_t stream);
 
 }  // namespace gpl1
+
+namespace gpl1 {
+// Shared-K multi-right-hand-side form (shared_k.cu).
+size_t mr_state_bytes();
+cudaError_t launch_mr_init(const float* Y, long long ldy, float* X, long long ldx, uint16_t* Rs, int n, int p,
+                           const double* rho, const double* fstar, void* states, const SolveParams& prm, int nrhs,
+                           cudaStream_t s);
+cudaError_t launch_mr_phase_p(const float* G, const float* Gprev, const float* X, long long ldx, float* D,
+                              uint16_t* DXs, int p, int nrhs, int k, void* states, const SolveParams& prm,
+                              cudaStream_t s);
+cudaError_t launch_mr_phase_l(const float* KDX, const void* Kt, const float* Y, long long ldy, float* X,
+                              long long ldx, const float* D, uint16_t* Rs, int n, int p, int nrhs, int k,
+                              void* states, const SolveParams& prm, gpl1_result* res, int* done_count,
+                              cudaStream_t s);
+cudaError_t launch_transpose_bf16(const void* K, long long ldk, void* Kt, int n, int p, cudaStream_t s);
+}  // namespace gpl1

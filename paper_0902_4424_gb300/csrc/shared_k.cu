@@ -1,0 +1,562 @@
+// Shared-K form of Alg. GP + SS: nrhs instances of eq. 2 that share one K
+// (BF16) and differ in y and rho, solved together.  Their gradients
+// g_b = 2 K^T r_b and their products K d_b, K x_b are then the matrix products
+//
+//   G   = 2 R K        (nrhs x p)   on the tensor cores as  K^T [R]^T
+//   KDX = [D; X] K^T   (2 nrhs x n) on the tensor cores as  K [D; X]^T
+//
+// (gemm_tc.cu), with the FP32 vectors carried as three BF16 terms
+// (hi + mid + lo = the FP32 value to 2^-24), so a BF16 K gives FP32-accurate
+// products.  Everything else of an iteration is per instance and runs in two
+// "column" kernels, one CTA per instance:
+//
+//   mr_phase_p: z^T z, g^T x, ||g||_inf; Alg. SS; v = x - alpha g; the
+//     projection threshold (block_l1_tau_fixed_point, as in the single solve);
+//     d = P(v) - x; g^T d, ||d||^2; the BF16 terms of d and x for the second
+//     product.
+//   mr_phase_l: f, r^T K d, ||K d||^2 from K x and K d; the Armijo test of
+//     Alg. GP on the exact expansion (FP64, lead thread); x += lam d,
+//     r += lam K d and its BF16 terms for the next gradient; Alg. SS state;
+//     the stop rules.
+//
+// Near the stop (estimated gap below 1000 tol, or progress below 1e-4 f),
+// mr_phase_l forms K x itself instead of taking it from the tensor-core
+// product: the FP32 accumulation over 3p terms there leaves about 1e-6 of
+// |K x| in each entry, which r^T dKx turns into an error of f far above
+// tol f* when f* << ||y||^2.  The iterate is sparse by then (the l1 ball), so
+// K x = sum over the support of x_j (column j of K = row j of the stored K^T),
+// with exact products and two-sums: the same compensated sum as the single
+// solve's pass B near its stop.
+//
+// As in the single solve, x is kept inside the ball (an exact ||x||_1 check
+// and a scale back onto the ball when rounding leaves it outside) and tau is
+// recomputed on the active set from x and g, so d stays a descent direction.
+#include <cudaTypedefs.h>
+
+#include "launch.h"
+
+namespace gpl1 {
+
+constexpr int kMrVmax = 35;   // p <= 35 * 480
+
+struct MrState {
+  SSState<float> ss;
+  float ah, th, tl, vbound, gmaxf, xscale;
+  float rho_hi, rho_lo;
+  int inside, nz, iters, backtracks, stop, status, done, acc;
+  double f_cur, gap_den, f_star, rho, lam, gd, dd, gx;
+  double fhist[kMaxM];
+};
+
+struct MrSmem {
+  float xs[kMrVmax * kConsumers];
+  ProjSmem ps;
+  Scratch sc;
+  int flag[4];
+};
+
+size_t mr_state_bytes() { return sizeof(MrState); }
+
+__device__ __forceinline__ void split3(float v, uint16_t& h, uint16_t& m, uint16_t& l) {
+  const __nv_bfloat16 bh = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(bh);   // exact
+  const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(bm);  // exact
+  const __nv_bfloat16 bl = __float2bfloat16_rn(r2);
+  h = __bfloat16_as_ushort(bh);
+  m = __bfloat16_as_ushort(bm);
+  l = __bfloat16_as_ushort(bl);
+}
+
+// Alg. SS for k >= 1 (the same rule as the single solve): alpha from BB1/BB2
+// with the ratio test against tau_k and the alpha^(2) window.
+__device__ float mr_ss_step(SSState<float>& st, float zz, const SolveParams& P) {
+  const float amin_p = static_cast<float>(P.alpha_min), amax_p = static_cast<float>(P.alpha_max);
+  float alpha, a2_this;
+  if (st.sz_prev <= 0.f) {
+    alpha = amax_p;
+    a2_this = amax_p;
+  } else {
+    const float a1 = fminf(fmaxf(st.ss_prev / st.sz_prev, amin_p), amax_p);
+    const float a2 = fminf(fmaxf(st.sz_prev / zz, amin_p), amax_p);
+    a2_this = a2;
+    float amin = a2;
+    for (int q = 0; q < st.a2cnt && q < P.M_alpha; ++q) amin = fminf(amin, st.a2win[q]);
+    if (a2 <= st.tau_ss * a1) {
+      alpha = amin;
+      st.tau_ss *= 0.9f;
+    } else {
+      alpha = a1;
+      st.tau_ss *= 1.1f;
+    }
+  }
+  for (int q = P.M_alpha - 1; q > 0; --q) st.a2win[q] = st.a2win[q - 1];
+  if (P.M_alpha > 0) st.a2win[0] = a2_this;
+  if (st.a2cnt < P.M_alpha) ++st.a2cnt;
+  return alpha;
+}
+
+// Initial state, x0 = 0, r0 = -y: its BF16 terms for the first gradient.
+__global__ void __launch_bounds__(kConsumers) mr_init(const float* Y, long long ldy, float* X, long long ldx,
+                                                      uint16_t* Rs, int n, int p, const double* rho,
+                                                      const double* fstar, MrState* st, SolveParams prm) {
+  const int b = blockIdx.x, tid = threadIdx.x;
+  __shared__ Scratch sc;
+  const float* y = Y + b * ldy;
+  float* x = X + b * ldx;
+  uint16_t* rs = Rs + static_cast<long long>(b) * 3 * n;
+  for (int j = tid; j < p; j += kConsumers) x[j] = 0.f;
+  F2 yy{0.f, 0.f};
+  for (int i = tid; i < n; i += kConsumers) {
+    const float r = -y[i];
+    yy = f2_fma(yy, r, r);
+    uint16_t h, m, l;
+    split3(r, h, m, l);
+    rs[i] = h;
+    rs[n + i] = m;
+    rs[2 * n + i] = l;
+  }
+  F2 v[1] = {yy};
+  unsigned dummy = 0;
+  lead_reduce<1>(v, dummy, sc);
+  if (tid == 0) {
+    MrState s;
+    memset(&s, 0, sizeof s);
+    s.ss.tau_ss = static_cast<float>(prm.tau1);
+    const double y2 = as_double(v[0]);
+    s.f_cur = y2;
+    for (int q = 0; q < kMaxM; ++q) s.fhist[q] = y2;
+    s.rho = rho[b];
+    const F2 rp = f2_of(rho[b]);
+    s.rho_hi = rp.hi;
+    s.rho_lo = rp.lo;
+    s.f_star = fstar ? fstar[b] : -1.0;
+    s.gap_den = fmax(s.f_star, prm.tol * y2);
+    s.xscale = 1.f;
+    s.stop = GPL1_STOP_MAX_ITER;
+    st[b] = s;
+  }
+}
+
+// d_j from the float pair of alpha (hi only here) and tau, as in pass B of the
+// single solve: the active form never subtracts x from a number of its size.
+__device__ __forceinline__ float mr_dir(float x, float g, float ah, float th, float tl, int inside) {
+  const float v = fmaf(-ah, g, x);
+  if (inside) return -ah * g;
+  if (!((fabsf(v) - th) > tl)) return -x;
+  const float s = v > 0.f ? 1.f : -1.f;
+  const float pr = __fmul_rn(ah, g);
+  const float e = fmaf(ah, g, -pr);
+  const F2 q = two_sum(pr, th * s);
+  return -(q.hi + (q.lo + (e + tl * s)));
+}
+
+__global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const float* Gprev, const float* X,
+                                                         long long ldx, float* D, uint16_t* DXs, int p, int nrhs,
+                                                         int k, MrState* st, SolveParams prm) {
+  const int b = blockIdx.x, tid = threadIdx.x;
+  MrState& S = st[b];
+  if (S.done) return;   // the same value in every thread of the CTA
+  extern __shared__ uint8_t mr_raw[];
+  MrSmem& sm = *reinterpret_cast<MrSmem*>(mr_raw);
+  float* const xs = sm.xs;
+  const int neu = (p + kConsumers - 1) / kConsumers;
+  const float* g = G + static_cast<long long>(b) * p;
+  const float* gp = Gprev + static_cast<long long>(b) * p;
+  const float* x = X + b * ldx;
+  // z^T z, g^T x, max |g|, ||x||_1
+  F2 zz{0.f, 0.f}, gx{0.f, 0.f}, l1{0.f, 0.f};
+  float pm = 0.f;
+  for (int e = 0; e < neu; ++e) {
+    const int j = tid + e * kConsumers;
+    float xv = 0.f;
+    if (j < p) {
+      const float gv = g[j];
+      xv = x[j];
+      if (k > 0) {
+        const float z = gv - gp[j];
+        zz = f2_fma(zz, z, z);
+      }
+      gx = f2_fma(gx, gv, xv);
+      l1 = f2_add(l1, fabsf(xv));
+      pm = fmaxf(pm, fabsf(gv));
+    }
+    xs[e * kConsumers + tid] = xv;
+  }
+  F2 red[3] = {zz, gx, l1};
+  unsigned mx = __float_as_uint(pm);
+  lead_reduce<3>(red, mx, sm.sc);
+  if (tid == 0) {
+    S.gmaxf = __uint_as_float(mx);
+    S.gx = as_double(red[1]);
+    const F2 rp{S.rho_hi, S.rho_lo};
+    const float ex = (red[2].hi - rp.hi) + (red[2].lo - rp.lo);   // ||x||_1 - rho
+    S.xscale = ex > 0.f ? __fdiv_rd(rp.hi, red[2].hi) * (1.f - 0x1p-21f) : 1.f;
+    int fin = 0;
+    if (prm.stop_rule & GPL1_STOP_ON_FW) {
+      const double fw = S.gx + S.rho * static_cast<double>(S.gmaxf);
+      if (fw <= prm.tol * (S.f_cur - fw)) {
+        S.stop = GPL1_STOP_FW;
+        S.done = 1;
+        fin = 1;
+      }
+    }
+    if (!fin && k > 0) {
+      S.ah = mr_ss_step(S.ss, red[0].hi + red[0].lo, prm);
+      S.vbound = (S.rho_hi + S.ah * S.gmaxf) * 1.00001f;
+    }
+    if (!fin && k == 0) S.vbound = (S.rho_hi + S.gmaxf) * 1.00001f;
+    sm.flag[0] = fin;
+  }
+  consumer_sync();
+  if (sm.flag[0]) return;
+  const float xsc = S.xscale;
+  const F2 rho_p{S.rho_hi, S.rho_lo};
+  if (k == 0) {   // alpha_0 = clamp(1 / ||P(x0 - g0)||_inf)  (rule 1: of P(.) - x0)
+    for (int e = 0; e < neu; ++e) {
+      const int j = tid + e * kConsumers;
+      xs[e * kConsumers + tid] = j < p ? fmaf(-1.f, g[j], xs[e * kConsumers + tid] * xsc) : 0.f;
+    }
+    consumer_sync();
+    const SmemAcc<float, kMrVmax> acc{xs, neu};
+    const TauResult tw = block_l1_tau_fixed_point<float>(acc, S.rho, rho_p, 0.f, sm.ps, sm.sc, S.vbound);
+    const TauPair tp{tw.th, tw.tl};
+    float m = 0.f;
+    for (int e = 0; e < neu; ++e) {
+      const int j = tid + e * kConsumers;
+      if (j >= p) break;
+      const float v = xs[e * kConsumers + tid];
+      const float a = fabsf(v);
+      float h = tw.inside ? v : (tp.below(a) ? 0.f : copysignf((a - tp.hi) - tp.lo, v));
+      if (prm.alpha0_rule == 1) h -= x[j] * xsc;
+      m = fmaxf(m, fabsf(h));
+    }
+    m = block_max_nonneg(m, sm.sc);
+    if (tid == 0) {
+      const double a0 = m > 0.f ? fmin(fmax(1.0 / static_cast<double>(m), prm.alpha_min), prm.alpha_max)
+                                : prm.alpha_max;
+      S.ah = static_cast<float>(a0);
+      S.vbound = (S.rho_hi + S.ah * S.gmaxf) * 1.00001f;
+    }
+    consumer_sync();
+  }
+  const float ah = S.ah;
+  for (int e = 0; e < neu; ++e) {
+    const int j = tid + e * kConsumers;
+    xs[e * kConsumers + tid] = j < p ? fmaf(-ah, g[j], x[j] * xsc) : 0.f;
+  }
+  consumer_sync();
+  const SmemAcc<float, kMrVmax> vacc{xs, neu};
+  const TauResult tv = block_l1_tau_fixed_point<float>(vacc, S.rho, rho_p, S.th, sm.ps, sm.sc, S.vbound);
+  float th = tv.th, tl = tv.tl;
+  if (!tv.inside) {
+    // tau on the active set from x and g themselves (see the file comment)
+    const TauPair tp{th, tl};
+    F2 v3[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int e = 0; e < neu; ++e) {
+      const int j = tid + e * kConsumers;
+      const float vv = xs[e * kConsumers + tid];
+      if (j < p && !tp.below(fabsf(vv))) {
+        const float s = vv > 0.f ? 1.f : -1.f;
+        v3[0] = f2_add(v3[0], s * (x[j] * xsc));
+        v3[1] = f2_add(v3[1], s * g[j]);
+        v3[2] = f2_add(v3[2], 1.f);
+      }
+    }
+    unsigned dummy = 0;
+    lead_reduce<3>(v3, dummy, sm.sc);
+    if (tid == 0) {
+      const float c = v3[2].hi;
+      const float ph = __fmul_rn(ah, v3[1].hi);
+      const float pl = fmaf(ah, v3[1].hi, -ph) + ah * v3[1].lo;
+      F2 t = f2_add(v3[0], F2{-ph, -pl});
+      t = f2_add(t, F2{-rho_p.hi, -rho_p.lo});
+      const float q1 = __fdiv_rn(t.hi, c);
+      const float rem = fmaf(-q1, c, t.hi) + t.lo;
+      const F2 q = two_sum(q1, __fdiv_rn(rem, c));
+      sm.sc.tp[2] = (c > 0.f && q.hi > 0.f) ? q.hi : th;
+      sm.sc.tp[3] = (c > 0.f && q.hi > 0.f) ? q.lo : tl;
+    }
+    consumer_sync();
+    th = sm.sc.tp[2];
+    tl = sm.sc.tp[3];
+  }
+  // direction, its sums, and the BF16 terms of d and x for K [D; X]^T
+  float* d = D + static_cast<long long>(b) * p;
+  uint16_t* dd_s = DXs + static_cast<long long>(b) * 3 * p;
+  uint16_t* xx_s = DXs + static_cast<long long>(nrhs + b) * 3 * p;
+  F2 sgd{0.f, 0.f}, sdd{0.f, 0.f};
+  unsigned nz = 0;
+  for (int j = tid; j < p; j += kConsumers) {
+    const float xj = x[j] * xsc, gj = g[j];
+    const float dj = mr_dir(xj, gj, ah, th, tl, tv.inside);
+    d[j] = dj;
+    sgd = f2_fma(sgd, gj, dj);
+    sdd = f2_fma(sdd, dj, dj);
+    nz |= dj != 0.f ? 1u : 0u;
+    uint16_t h, m, l;
+    split3(dj, h, m, l);
+    dd_s[j] = h;
+    dd_s[p + j] = m;
+    dd_s[2 * p + j] = l;
+    split3(xj, h, m, l);
+    xx_s[j] = h;
+    xx_s[p + j] = m;
+    xx_s[2 * p + j] = l;
+  }
+  F2 v2[2] = {sgd, sdd};
+  unsigned nzm = nz;
+  lead_reduce<2>(v2, nzm, sm.sc);
+  if (tid == 0) {
+    S.gd = as_double(v2[0]);
+    S.dd = as_double(v2[1]);
+    S.nz = nzm ? 1 : 0;
+    S.th = th;
+    S.tl = tl;
+    S.inside = tv.inside;
+  }
+}
+
+constexpr int kMrSupport = 2048;   // support entries kept for the accurate K x
+constexpr int kMrRowsPerThread = 9; // n <= 9 * 480 rows for the accurate K x
+
+__global__ void __launch_bounds__(kConsumers) mr_phase_l(const float* KDX, const uint16_t* Kt, const float* Y,
+                                                         long long ldy, float* X, long long ldx, const float* D,
+                                                         uint16_t* Rs, int n, int p, int nrhs, int k, MrState* st,
+                                                         SolveParams prm, gpl1_result* res, int* done_count) {
+  const int b = blockIdx.x, tid = threadIdx.x;
+  MrState& S = st[b];
+  __shared__ Scratch sc;
+  __shared__ int flag[2];
+  __shared__ float lamf;
+  __shared__ int sup_j[kMrSupport];
+  __shared__ float sup_x[kMrSupport];
+  __shared__ int sup_n;
+  if (S.done) {   // stopped in phase P of this iteration (FW) or earlier
+    if (tid == 0 && S.done == 1) {
+      S.done = 2;   // record once
+      gpl1_result r{};
+      r.status = S.status;
+      r.stop = S.stop;
+      r.iters = S.iters;
+      r.backtracks = S.backtracks;
+      r.f = S.f_cur;
+      r.rel_gap = S.f_star > 0.0 ? (S.f_cur - S.f_star) / S.f_star : -1.0;
+      r.fw_gap = S.gx + S.rho * static_cast<double>(S.gmaxf);
+      r.lambda = 0.5 * static_cast<double>(S.gmaxf);
+      r.alpha = S.ah;
+      r.tau = static_cast<double>(S.th) + static_cast<double>(S.tl);
+      r.fail_iter = S.iters;
+      res[b] = r;
+      atomicAdd(done_count, 1);
+    }
+    return;
+  }
+  const float* kd = KDX + static_cast<long long>(b) * n;
+  const float* kx = KDX + static_cast<long long>(nrhs + b) * n;
+  const float* y = Y + b * ldy;
+  // r = K x - y: from the tensor-core product, or near the stop summed exactly
+  // over the support of x (the iterate scaled into the ball, as phase P used it)
+  bool exact = S.acc && n <= kMrRowsPerThread * kConsumers;
+  if (exact) {
+    if (tid == 0) sup_n = 0;
+    __syncthreads();
+    const float* x = X + b * ldx;
+    const float xsc = S.xscale;
+    for (int j = tid; j < p; j += kConsumers) {
+      const float xv = x[j] * xsc;
+      if (xv != 0.f) {
+        const int q = atomicAdd(&sup_n, 1);
+        if (q < kMrSupport) {
+          sup_j[q] = j;
+          sup_x[q] = xv;
+        }
+      }
+    }
+    __syncthreads();
+    exact = sup_n <= kMrSupport;   // the same decision in every thread
+  }
+  F2 racc[kMrRowsPerThread];
+  if (exact) {
+#pragma unroll
+    for (int m = 0; m < kMrRowsPerThread; ++m) racc[m] = F2{0.f, 0.f};
+    const int ns = sup_n;
+    for (int q = 0; q < ns; ++q) {
+      const float xv = sup_x[q];
+      const uint16_t* col = Kt + static_cast<long long>(sup_j[q]) * n;   // column j of K
+#pragma unroll
+      for (int m = 0; m < kMrRowsPerThread; ++m) {
+        const int i = tid + m * kConsumers;
+        if (i < n) racc[m] = f2_fma(racc[m], __uint_as_float(static_cast<unsigned>(col[i]) << 16), xv);
+      }
+    }
+  }
+  F2 v[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int i = tid, m = 0; i < n; i += kConsumers, ++m) {
+    const float kdi = kd[i];
+    F2 r;
+    if (exact) {
+      const F2 t = two_sum(racc[m].hi, -y[i]);
+      r = two_sum(t.hi, t.lo + racc[m].lo);
+    } else {
+      r = two_sum(kx[i], -y[i]);
+    }
+    v[0] = f2_fma(v[0], r.hi, r.hi + 2.f * r.lo);
+    v[1] = f2_fma(v[1], r.hi + r.lo, kdi);
+    v[2] = f2_fma(v[2], kdi, kdi);
+  }
+  unsigned dummy = 0;
+  lead_reduce<3>(v, dummy, sc);
+  if (tid == 0) {
+    // Alg. GP, Steps 4-6, on f(x + lam d) = f + lam g^T d + lam^2 ||K d||^2 (FP64)
+    const double fk = as_double(v[0]), kb2 = as_double(v[2]), gd = S.gd;
+    int acc = 0;
+    double lam = 1.0, fnext = fk;
+    if (!S.nz) {
+      S.stop = GPL1_STOP_STATIONARY;
+      S.f_cur = fk;
+      S.done = 1;
+    } else if (!isfinite(fk) || !isfinite(kb2) || !isfinite(gd)) {
+      S.status = GPL1_ERR_NONFINITE;
+      S.stop = GPL1_STOP_ERROR;
+      S.done = 1;
+    } else {
+      S.fhist[0] = fk;
+      double fmaxv = fk;
+      for (int q = 1; q < prm.M && q <= k; ++q) fmaxv = fmax(fmaxv, S.fhist[q]);
+      int bt = 0;
+      for (;;) {
+        if ((fk - fmaxv) + lam * (gd + lam * kb2) <= prm.beta * lam * gd) {
+          acc = 1;
+          break;
+        }
+        if (bt >= prm.max_backtracks) break;
+        lam *= prm.theta;
+        ++bt;
+      }
+      S.backtracks += bt;
+      if (!acc) {
+        S.status = GPL1_ERR_LINESEARCH;
+        S.stop = GPL1_STOP_ERROR;
+        S.f_cur = fk;
+        S.done = 1;
+      } else {
+        fnext = fk + lam * (gd + lam * kb2);
+        for (int q = kMaxM - 1; q > 0; --q) S.fhist[q] = S.fhist[q - 1];
+        S.fhist[0] = fnext;
+        S.lam = lam;
+        const float lf = static_cast<float>(lam);
+        S.ss.ss_prev = lf * lf * static_cast<float>(S.dd);
+        S.ss.sz_prev = 2.f * lf * lf * static_cast<float>(kb2);
+        S.f_cur = fnext;
+        S.iters = k + 1;
+        if ((S.f_star >= 0.0 && fnext - S.f_star <= 1e3 * prm.tol * S.gap_den) || fk - fnext <= 1e-4 * fk) S.acc = 1;
+        if ((prm.stop_rule & GPL1_STOP_ON_REL_GAP) && S.f_star >= 0.0 && fnext - S.f_star <= prm.tol * S.gap_den) {
+          S.stop = GPL1_STOP_REL_GAP;
+          S.done = 1;
+        } else if (S.iters >= prm.max_iter) {
+          S.stop = GPL1_STOP_MAX_ITER;
+          S.status = GPL1_ERR_NOT_CONVERGED;
+          S.done = 1;
+        }
+      }
+    }
+    if (!S.done) S.iters = k + 1;
+    flag[0] = acc;
+    flag[1] = S.done;
+    lamf = static_cast<float>(lam);
+  }
+  __syncthreads();
+  if (flag[0]) {   // x += lam d (on the iterate scaled into the ball), r += lam K d
+    const float la = lamf, xsc = S.xscale;
+    float* x = X + b * ldx;
+    const float* d = D + static_cast<long long>(b) * p;
+    for (int j = tid; j < p; j += kConsumers) x[j] = fmaf(la, d[j], x[j] * xsc);
+    uint16_t* rs = Rs + static_cast<long long>(b) * 3 * n;
+    for (int i = tid, m = 0; i < n; i += kConsumers, ++m) {
+      F2 r;
+      if (exact) {
+        const F2 t = two_sum(racc[m].hi, -y[i]);
+        r = two_sum(t.hi, t.lo + racc[m].lo);
+      } else {
+        r = two_sum(kx[i], -y[i]);
+      }
+      const float rn = r.hi + fmaf(la, kd[i], r.lo);
+      uint16_t th3, tm3, tl3;
+      split3(rn, th3, tm3, tl3);
+      rs[i] = th3;
+      rs[n + i] = tm3;
+      rs[2 * n + i] = tl3;
+    }
+  }
+  if (flag[1] && tid == 0) {
+    S.done = 2;
+    gpl1_result r{};
+    r.status = S.status;
+    r.stop = S.stop;
+    r.iters = S.iters;
+    r.backtracks = S.backtracks;
+    r.f = S.f_cur;
+    r.rel_gap = S.f_star > 0.0 ? (S.f_cur - S.f_star) / S.f_star : -1.0;
+    r.fw_gap = S.gx + S.rho * static_cast<double>(S.gmaxf);
+    r.lambda = 0.5 * static_cast<double>(S.gmaxf);
+    r.alpha = S.ah;
+    r.tau = static_cast<double>(S.th) + static_cast<double>(S.tl);
+    r.fail_iter = S.iters;
+    res[b] = r;
+    atomicAdd(done_count, 1);
+  }
+}
+
+// K^T (p x n) from K (n x ldk), BF16 bit patterns, 32 x 32 tiles.
+__global__ void transpose_bf16(const uint16_t* K, long long ldk, uint16_t* Kt, int n, int p) {
+  __shared__ uint16_t t[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, j = j0 + threadIdx.x;
+    t[r][threadIdx.x] = (i < n && j < p) ? K[i * ldk + j] : 0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, i = i0 + threadIdx.x;
+    if (j < p && i < n) Kt[static_cast<long long>(j) * n + i] = t[threadIdx.x][r];
+  }
+}
+
+size_t mr_phase_p_smem() { return sizeof(MrSmem); }
+
+cudaError_t launch_mr_init(const float* Y, long long ldy, float* X, long long ldx, uint16_t* Rs, int n, int p,
+                           const double* rho, const double* fstar, void* states, const SolveParams& prm, int nrhs,
+                           cudaStream_t s) {
+  mr_init<<<nrhs, kConsumers, 0, s>>>(Y, ldy, X, ldx, Rs, n, p, rho, fstar, static_cast<MrState*>(states), prm);
+  return cudaGetLastError();
+}
+cudaError_t launch_mr_phase_p(const float* G, const float* Gprev, const float* X, long long ldx, float* D,
+                              uint16_t* DXs, int p, int nrhs, int k, void* states, const SolveParams& prm,
+                              cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(mr_phase_p, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sizeof(MrSmem)));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  mr_phase_p<<<nrhs, kConsumers, sizeof(MrSmem), s>>>(G, Gprev, X, ldx, D, DXs, p, nrhs, k,
+                                                      static_cast<MrState*>(states), prm);
+  return cudaGetLastError();
+}
+cudaError_t launch_mr_phase_l(const float* KDX, const void* Kt, const float* Y, long long ldy, float* X,
+                              long long ldx, const float* D, uint16_t* Rs, int n, int p, int nrhs, int k,
+                              void* states, const SolveParams& prm, gpl1_result* res, int* done_count,
+                              cudaStream_t s) {
+  mr_phase_l<<<nrhs, kConsumers, 0, s>>>(KDX, static_cast<const uint16_t*>(Kt), Y, ldy, X, ldx, D, Rs, n, p, nrhs,
+                                         k, static_cast<MrState*>(states), prm, res, done_count);
+  return cudaGetLastError();
+}
+cudaError_t launch_transpose_bf16(const void* K, long long ldk, void* Kt, int n, int p, cudaStream_t s) {
+  const dim3 grid((p + 31) / 32, (n + 31) / 32), block(32, 8);
+  transpose_bf16<<<grid, block, 0, s>>>(static_cast<const uint16_t*>(K), ldk, static_cast<uint16_t*>(Kt), n, p);
+  return cudaGetLastError();
+}
+
+}  // namespace gpl1
