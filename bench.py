@@ -262,6 +262,74 @@ def run_batched(count, steps, dev):
     return out
 
 
+# ------------------------------------------------ shared-K form (c3b)
+def run_shared_k(nrhs, dev, verify=16, plain=8):
+    """Solves/s of nrhs right-hand sides on one K 2048 x 8192 BF16 (each from its own
+    +-1 102-sparse signal), all in one gpl1_solve_shared_k call (tensor-core GEMMs),
+    against the same instances solved one by one with gpl1_solve (plain form, a
+    sample).  Stops at relative gap 5e-7 against the oracle's optimum of each
+    instance (tests/golden/c3b_fstar.json); x is checked by the oracle on a sample."""
+    import torch
+
+    import oracle
+    import paper_0902_4424_gb300 as pkg
+    import workloads as W
+    with open(os.path.join(ROOT, "tests", "golden", "c3b_fstar.json")) as fh:
+        fstars = json.load(fh)["f_star"]
+    Ks, ldk, Y, rho, Xt = W.shared_k(nrhs=len(fstars))
+    Ks, Y, rho, Xt, fstars = Ks, Y[:nrhs], rho[:nrhs], Xt[:nrhs], fstars[:nrhs]
+    n, p = Ks.shape[0], Xt.shape[1]
+    K = torch.from_numpy(Ks.view(np.int16)).to(dev)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y)).to(dev)
+    ctx = pkg.Context(dev.index or 0)
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=0.5 * TOL, max_iter=2000)
+    ctx.solve_shared_k(K, Yd, rho, p=p, f_star=fstars, params=prm)          # warm-up
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    X, res = ctx.solve_shared_k(K, Yd, rho, p=p, f_star=fstars, params=prm)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    iters = [r.iters for r in res]
+    ok = sum(r.status == 0 for r in res)
+    Xh = X.double().cpu().numpy()
+    probs = [W.Problem(Ks, n, p, ldk, W.DT_BF16, Y[q].copy(), float(rho[q]), Xt[q], f"c3b_{q}") for q in range(nrhs)]
+    idx = np.linspace(0, nrhs - 1, min(verify, nrhs)).astype(int)
+    gaps = [(oracle.objective(probs[q], Xh[q]) - fstars[q]) / fstars[q] for q in idx]
+    # the plain form on a sample: each instance its own cooperative solve of K
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for q in range(plain):
+        ctx.solve(K, Yd[q], float(rho[q]), p=p, f_star=fstars[q], params=prm)
+    t1.record(stream)
+    t1.synchronize()
+    plain_ms = t0.elapsed_time(t1) / plain
+    # executed tensor-core work: per iteration 2 p nrhs 3n (K^T R) + 2 n 2nrhs 3p (K [D; X])
+    flops = 18.0 * n * p * nrhs * max(iters)
+    peaks_d = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks_d = json.load(fh)
+    except OSError:
+        pass
+    tf_peak = float(peaks_d.get("bf16_tflops", 1900.0))
+    out = {"workload": f"c3b_sharedK{n}x{p}_bf16_{nrhs}rhs", "instances": nrhs,
+           "solves_per_s": nrhs / (ms / 1e3), "ms_per_call": ms, "ok": ok,
+           "iters_mean": statistics.mean(iters), "iters_max": max(iters),
+           "plain_solves_per_s": 1e3 / plain_ms, "plain_sample": plain,
+           "speedup_vs_plain": (nrhs / (ms / 1e3)) / (1e3 / plain_ms),
+           "stop": f"kernel stop rel_gap<={0.5 * TOL:g} vs oracle f* per instance",
+           "verified_max_rel_gap": max(gaps), "verified_instances": len(gaps),
+           "tensor_tflops": flops / (ms / 1e3) / 1e12,
+           "tensor_frac_of_measured_bf16": flops / (ms / 1e3) / 1e12 / tf_peak,
+           "note": "executed GEMM work incl. the 3-term BF16 split of the vector operand; all iterations of the call"}
+    ctx.close()
+    return out
+
+
 # -------------------------------------------------------------- GPU path
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -397,6 +465,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if args.batched_sample > 0:
         line["batched"] = run_batched(args.batched_sample, 3, dev)
+    if args.shared_k > 0 and os.path.exists(os.path.join(ROOT, "tests", "golden", "c3b_fstar.json")):
+        line["shared_k"] = run_shared_k(args.shared_k, dev)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -423,6 +493,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-sample", type=int, default=64,
                     help="also time this many ragged instances batched vs plain (0: skip)")
+    ap.add_argument("--shared-k", type=int, default=1024,
+                    help="also time this many right-hand sides on one shared K (0: skip)")
     ap.add_argument("--workload", choices=["c1", "c3a"], default="c1",
                     help="c3a: only the batched ragged form, all 512 instances")
     args = ap.parse_args()

@@ -6,6 +6,7 @@ no decrease of f for 30 iterations).  Nothing here touches the CUDA path.
 
     python tests/golden/make_golden.py [c0 c1 c2 ...]
     python tests/golden/make_golden.py c3a      # the ragged batch: c3a_fstar.json
+    python tests/golden/make_golden.py c3b      # the shared-K right-hand sides: c3b_fstar.json
 """
 import json
 import os
@@ -58,9 +59,29 @@ def main_c3a(count=512):
                    "solver": "oracle.floor_solve"}, fh, indent=0)
 
 
+def main_c3b(nrhs=1024):
+    """tests/golden/c3b_fstar.json: f* of each right-hand side of the shared-K
+    workload (K 2048 x 8192 BF16), by the oracle's floor solve."""
+    out = os.path.join(os.path.dirname(OUT), "c3b_fstar.json")
+    t = time.time()
+    Ks, ldk, Y, rho, X = W.shared_k(nrhs=nrhs)
+    n, p = Ks.shape[0], X.shape[1]
+    fs = []
+    for b in range(nrhs):
+        prob = W.Problem(Ks, n, p, ldk, W.DT_BF16, Y[b].copy(), float(rho[b]), X[b], f"c3b_{b}")
+        fs.append(oracle.floor_solve(prob)[1].f)
+        if b % 64 == 63:
+            print(b + 1, f"{time.time() - t:.0f}s", flush=True)
+    with open(out, "w") as fh:
+        json.dump({"workload": f"c3b_sharedK2048x8192_bf16_{nrhs}rhs", "f_star": fs,
+                   "solver": "oracle.floor_solve"}, fh, indent=0)
+
+
 if __name__ == "__main__":
     args = sys.argv[1:]
     if args == ["c3a"]:
         main_c3a()
+    elif args == ["c3b"]:
+        main_c3b()
     else:
         main(args or list(CONFIGS))
