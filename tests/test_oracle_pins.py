@@ -322,3 +322,70 @@ def test_golden_c3a_fstar_match_oracle():
         prob = W.ragged_instance(int(i), gold["n"][i])
         f = oracle.floor_solve(prob)[1].f
         assert abs(f - gold["f_star"][i]) <= 1e-12 * gold["f_star"][i]
+
+
+# ------------------------------------------------------- learned warm start
+from oracle import lista  # noqa: E402
+
+
+def eq1_optimality_residual(K, y, x, lam):
+    """How far x is from the optimality conditions of eq. 1 (min ||Kx-y||^2 + 2 lam ||x||_1):
+    c = K^T (y - K x) must equal lam sgn(x) on the support and satisfy |c| <= lam off it."""
+    c = K.T @ (y - K @ x)
+    on = x != 0
+    r_on = np.max(np.abs(c[on] - lam * np.sign(x[on]))) if on.any() else 0.0
+    r_off = max(0.0, np.max(np.abs(c[~on])) - lam) if (~on).any() else 0.0
+    return max(r_on, r_off)
+
+
+def test_lista_one_layer_on_orthonormal_k_solves_eq1():
+    rng = np.random.default_rng(31)
+    n, p = 40, 16
+    K, _ = np.linalg.qr(rng.standard_normal((n, p)))
+    y = rng.standard_normal((3, n))
+    lam = 0.3
+    xs, _ = lista.forward(K, K.T[None], np.array([lam]), y)
+    for b in range(3):
+        assert eq1_optimality_residual(K, y[b], xs[1][b], lam) <= 1e-12
+
+
+def test_lista_tied_ista_layers_reach_eq1_optimality():
+    rng = np.random.default_rng(32)
+    n, p = 30, 60
+    K = rng.standard_normal((n, p)) / np.sqrt(n)
+    y = rng.standard_normal((2, n))
+    lam = 0.2
+    W, theta, Lk = lista.init_params(K, 1, lam)
+    assert abs(Lk - np.linalg.norm(K, 2) ** 2) <= 1e-6 * Lk   # power iteration, 200 steps
+    layers = 4000
+    xs, _ = lista.forward(K, np.repeat(W, layers, axis=0), np.full(layers, theta[0]), y)
+    # each layer is the proximal-gradient step of 1/2 ||Kx-y||^2 + lam ||x||_1 (step 1/L), whose
+    # minimiser is eq. 1's at the same lam (both have K^T (y - Kx) in lam d||x||_1)
+    for b in range(2):
+        assert eq1_optimality_residual(K, y[b], xs[-1][b], lam) <= 1e-6
+
+
+def test_lista_backward_matches_finite_differences():
+    rng = np.random.default_rng(33)
+    n, p, L, B = 6, 10, 3, 4
+    K = rng.standard_normal((n, p)) / np.sqrt(n)
+    Y = rng.standard_normal((B, n))
+    Xt = rng.standard_normal((B, p)) * (rng.random((B, p)) < 0.3)
+    W = rng.standard_normal((L, p, n)) * 0.3
+    theta = np.array([0.05, 0.08, 0.03])
+    f0, dW, dth = lista.backward(K, W, theta, Y, Xt)
+    h = 1e-6
+    for (l, i, j) in [(0, 0, 0), (1, 3, 2), (2, 9, 5), (0, 5, 4), (2, 1, 1)]:
+        Wp, Wm = W.copy(), W.copy()
+        Wp[l, i, j] += h
+        Wm[l, i, j] -= h
+        fp = lista.loss(lista.forward(K, Wp, theta, Y)[0][-1], Xt)
+        fm = lista.loss(lista.forward(K, Wm, theta, Y)[0][-1], Xt)
+        assert abs((fp - fm) / (2 * h) - dW[l, i, j]) <= 1e-6 * max(1.0, abs(dW[l, i, j]))
+    for l in range(L):
+        tp, tm = theta.copy(), theta.copy()
+        tp[l] += h
+        tm[l] -= h
+        fp = lista.loss(lista.forward(K, W, tp, Y)[0][-1], Xt)
+        fm = lista.loss(lista.forward(K, W, tm, Y)[0][-1], Xt)
+        assert abs((fp - fm) / (2 * h) - dth[l]) <= 1e-6 * max(1.0, abs(dth[l]))
