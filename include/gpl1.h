@@ -205,6 +205,38 @@ gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long long n, long 
                                 float* X, long long ldx, int nrhs, const gpl1_params* prm,
                                 gpl1_result* res);
 
+/* Learned warm start: an unrolled, learned version of the ISTA iteration of
+ * Sec. 2 (soft-thresholded Landweber steps),
+ *   x^0 = 0,  x^{l+1} = S_{theta_l}(x^l + W_l (y - K x^l)),  l < layers,
+ * for a batch of B right-hand sides (rows of Y, B x n, row stride ldy); its
+ * output, projected onto the l1 ball, is a starting point x0 for Alg. GP.
+ * K: GPL1_BF16 n x p (row stride ldk).  W: device FP32, layers x p x n (each
+ * layer row-major p x n).  theta: device FP32, layers.  The products run on
+ * the tensor cores in BF16 with FP32 accumulation (gpl1_gemm_bf16); n, p and
+ * B must be multiples of 64.  All three calls synchronise the context stream.
+ *   gpl1_lista_forward: X (device, B x p, row stride ldx) = x^layers.
+ *   gpl1_lista_grad: the loss mean_b ||x^layers_b - Xt_b||^2 (host double) and
+ *     its gradients dW (device FP32, like W) and dtheta (device FP32, layers);
+ *     the soft threshold contributes the subgradient 1[|z| > theta].
+ *   gpl1_lista_train: `steps` Adam updates (bias-corrected, beta 0.9/0.999,
+ *     step numbers t0+1 ..) of W (rate lr) and theta (rate lr_theta), step s
+ *     on rows (s mod (N / batch)) * batch .. + batch of (Y, Xt); adam_m,
+ *     adam_v: device FP32 moments of layers*p*n + layers entries (W, then
+ *     theta); losses: host array of `steps` doubles, the loss before each
+ *     update. */
+gpl1_status gpl1_lista_forward(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
+                               int layers, const float* W, const float* theta, const float* Y,
+                               long long ldy, long long B, float* X, long long ldx);
+gpl1_status gpl1_lista_grad(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
+                            int layers, const float* W, const float* theta, const float* Y, long long ldy,
+                            long long B, const float* Xt, long long ldt, float* dW, float* dtheta,
+                            double* loss);
+gpl1_status gpl1_lista_train(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
+                             int layers, float* W, float* theta, float* adam_m, float* adam_v,
+                             const float* Y, long long ldy, const float* Xt, long long ldt, long long N,
+                             long long batch, int steps, int t0, float lr, float lr_theta,
+                             double* losses);
+
 /* ---- Solve without allocating (an addition of this library; the paper has
  * no counterpart).
  *

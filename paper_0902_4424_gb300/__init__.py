@@ -30,7 +30,7 @@ ALGORITHMIC = (0, 3, 4, 5, 6)
 
 EXPORTS = ["gpl1_create", "gpl1_destroy", "gpl1_set_stream", "gpl1_last_error", "gpl1_params_default",
            "gpl1_project", "gpl1_solve", "gpl1_solve_batched", "gpl1_solve_noalloc", "gpl1_gemm_bf16",
-           "gpl1_solve_shared_k"]
+           "gpl1_solve_shared_k", "gpl1_lista_forward", "gpl1_lista_grad", "gpl1_lista_train"]
 
 
 class Gpl1Error(RuntimeError):
@@ -98,6 +98,12 @@ def lib():
                                           ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                           ctypes.POINTER(Params), ctypes.POINTER(Result)]
+        vp, ll, ci, cf = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_float
+        L.gpl1_lista_forward.argtypes = [vp, vp, ll, ll, ll, ci, vp, vp, vp, ll, ll, vp, ll]
+        L.gpl1_lista_grad.argtypes = [vp, vp, ll, ll, ll, ci, vp, vp, vp, ll, ll, vp, ll, vp, vp,
+                                      ctypes.POINTER(ctypes.c_double)]
+        L.gpl1_lista_train.argtypes = [vp, vp, ll, ll, ll, ci, vp, vp, vp, vp, vp, ll, vp, ll, ll, ll, ci, ci, cf, cf,
+                                       vp]
         L.gpl1_solve_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, ctypes.POINTER(Params),
                                          ctypes.POINTER(Result), ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]
         _lib = L
@@ -203,6 +209,50 @@ class Context:
                                   ctypes.c_void_p(out.data_ptr()), out.stride(0), float(scale))
         self._check(st)
         return out
+
+    # ------------------------------------------------ learned warm start
+    @staticmethod
+    def _ptr(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    def lista_forward(self, K, W, theta, Y, p=None, X=None):
+        """gpl1_lista_forward: x^L (B, p) float32 for right-hand sides Y (B, n)."""
+        import torch
+        n, ldk = K.shape
+        layers, pp, nn = W.shape
+        p = pp if p is None else int(p)
+        B = Y.shape[0]
+        X = torch.empty(B, p, dtype=torch.float32, device=Y.device) if X is None else X
+        self._bind_stream()
+        self._check(lib().gpl1_lista_forward(self._h, self._ptr(K), n, p, ldk, layers, self._ptr(W), self._ptr(theta),
+                                             self._ptr(Y), Y.stride(0), B, self._ptr(X), X.stride(0)))
+        return X
+
+    def lista_grad(self, K, W, theta, Y, Xt):
+        """gpl1_lista_grad: (loss, dW, dtheta) of mean ||x^L - Xt||^2 over the batch."""
+        import torch
+        n, ldk = K.shape
+        layers, p, _ = W.shape
+        dW = torch.empty_like(W)
+        dth = torch.empty_like(theta)
+        loss = ctypes.c_double()
+        self._bind_stream()
+        self._check(lib().gpl1_lista_grad(self._h, self._ptr(K), n, p, ldk, layers, self._ptr(W), self._ptr(theta),
+                                          self._ptr(Y), Y.stride(0), Y.shape[0], self._ptr(Xt), Xt.stride(0),
+                                          self._ptr(dW), self._ptr(dth), ctypes.byref(loss)))
+        return loss.value, dW, dth
+
+    def lista_train(self, K, W, theta, m, v, Y, Xt, batch, steps, t0=0, lr=1e-3, lr_theta=1e-3):
+        """gpl1_lista_train: `steps` Adam updates of W, theta in place; returns the losses."""
+        n, ldk = K.shape
+        layers, p, _ = W.shape
+        losses = (ctypes.c_double * steps)()
+        self._bind_stream()
+        self._check(lib().gpl1_lista_train(self._h, self._ptr(K), n, p, ldk, layers, self._ptr(W), self._ptr(theta),
+                                           self._ptr(m), self._ptr(v), self._ptr(Y), Y.stride(0), self._ptr(Xt),
+                                           Xt.stride(0), Y.shape[0], batch, steps, t0, float(lr), float(lr_theta),
+                                           ctypes.cast(losses, ctypes.c_void_p)))
+        return list(losses)
 
     # -------------------------------------------------------------- solve
     @staticmethod

@@ -715,3 +715,124 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
   if (worst != GPL1_OK) return fail(ctx, static_cast<gpl1_status>(worst), "an instance failed (status %d)", worst);
   return GPL1_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Learned warm start (lista.cu).
+
+namespace {
+
+gpl1_status ensure_encode(gpl1_ctx* ctx) {
+  if (ctx->encode) return GPL1_OK;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  GPL1_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q),
+            "cudaGetDriverEntryPointByVersion");
+  if (q != cudaDriverEntryPointSuccess || !fn) return fail(ctx, GPL1_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  ctx->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return GPL1_OK;
+}
+
+gpl1_status check_lista(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk, int layers,
+                        long long B) {
+  if (!K) return fail(ctx, GPL1_ERR_INVALID_ARG, "K is NULL");
+  if (layers < 1 || layers > 64) return fail(ctx, GPL1_ERR_INVALID_ARG, "layers must lie in [1, 64]");
+  if (n < 64 || p < 64 || B < 64 || n % 64 || p % 64 || B % 64)
+    return fail(ctx, GPL1_ERR_UNSUPPORTED, "n, p and the batch must be multiples of 64");
+  if (ldk < p || (ldk * 2) % 16 || reinterpret_cast<uintptr_t>(K) % 16)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "K rows must be 16-byte aligned, ldk >= p");
+  if (n > (1LL << 20) || p > (1LL << 20) || B > (1LL << 20)) return fail(ctx, GPL1_ERR_UNSUPPORTED, "too large");
+  return GPL1_OK;
+}
+
+gpl1_status lista_status(gpl1_ctx* ctx, int r, int* gerr) {
+  if (r == -1) return fail(ctx, GPL1_ERR_CUDA, "tensor map encoding failed");
+  if (r != 0) return cuda_fail(ctx, static_cast<cudaError_t>(r), "learned warm start");
+  int ge = 0;
+  GPL1_CUDA(cudaMemcpyAsync(&ge, gerr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "cudaMemcpyAsync");
+  GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "learned warm start");
+  if (ge) return fail(ctx, static_cast<gpl1_status>(ge), "a bounded wait in a GEMM ran out");
+  return GPL1_OK;
+}
+
+}  // namespace
+
+extern "C" gpl1_status gpl1_lista_forward(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
+                                          int layers, const float* W, const float* theta, const float* Y,
+                                          long long ldy, long long B, float* X, long long ldx) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  gpl1_status st = check_lista(ctx, K, n, p, ldk, layers, B);
+  if (st) return st;
+  if (!W || !theta || !Y || !X || ldy < n || ldx < p) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad pointer or stride");
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if ((st = ensure_encode(ctx))) return st;
+  if ((st = ensure_ws(ctx, 256 + lista_ws_bytes(layers, n, p, B)))) return st;
+  uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
+  int* gerr = reinterpret_cast<int*>(ws);
+  GPL1_CUDA(cudaMemsetAsync(gerr, 0, sizeof(int), ctx->stream), "cudaMemsetAsync");
+  const int r = lista_pass(ctx->encode, ws + 256, gerr, K, n, p, ldk, layers, W, true, theta, Y, ldy, B, nullptr, 0,
+                           X, ldx, nullptr, nullptr, nullptr, ctx->stream);
+  return lista_status(ctx, r, gerr);
+}
+
+extern "C" gpl1_status gpl1_lista_grad(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
+                                       int layers, const float* W, const float* theta, const float* Y, long long ldy,
+                                       long long B, const float* Xt, long long ldt, float* dW, float* dtheta,
+                                       double* loss) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  gpl1_status st = check_lista(ctx, K, n, p, ldk, layers, B);
+  if (st) return st;
+  if (!W || !theta || !Y || !Xt || !dW || !dtheta || ldy < n || ldt < p)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "bad pointer or stride");
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if ((st = ensure_encode(ctx))) return st;
+  if ((st = ensure_ws(ctx, 256 + lista_ws_bytes(layers, n, p, B)))) return st;
+  uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
+  int* gerr = reinterpret_cast<int*>(ws);
+  double* dloss = reinterpret_cast<double*>(ws + 64);
+  GPL1_CUDA(cudaMemsetAsync(ws, 0, 128, ctx->stream), "cudaMemsetAsync");
+  const int r = lista_pass(ctx->encode, ws + 256, gerr, K, n, p, ldk, layers, W, true, theta, Y, ldy, B, Xt, ldt,
+                           nullptr, 0, dW, dtheta, dloss, ctx->stream);
+  if (r == 0 && loss)
+    GPL1_CUDA(cudaMemcpyAsync(loss, dloss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "cudaMemcpyAsync");
+  return lista_status(ctx, r, gerr);
+}
+
+extern "C" gpl1_status gpl1_lista_train(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
+                                        int layers, float* W, float* theta, float* adam_m, float* adam_v,
+                                        const float* Y, long long ldy, const float* Xt, long long ldt, long long N,
+                                        long long batch, int steps, int t0, float lr, float lr_theta,
+                                        double* losses) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  gpl1_status st = check_lista(ctx, K, n, p, ldk, layers, batch);
+  if (st) return st;
+  if (!W || !theta || !adam_m || !adam_v || !Y || !Xt || ldy < n || ldt < p || N < batch || steps < 1 || t0 < 0)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "bad pointer, stride or count");
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if ((st = ensure_encode(ctx))) return st;
+  const size_t wcount = static_cast<size_t>(layers) * p * n;
+  const size_t grads = align_up((wcount + layers) * 4, 256);
+  const size_t lbytes = align_up(static_cast<size_t>(steps) * 8, 256);
+  if ((st = ensure_ws(ctx, 256 + grads + lbytes + lista_ws_bytes(layers, n, p, batch)))) return st;
+  uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
+  int* gerr = reinterpret_cast<int*>(ws);
+  float* dW = reinterpret_cast<float*>(ws + 256);
+  float* dth = dW + wcount;
+  double* dloss = reinterpret_cast<double*>(ws + 256 + grads);
+  uint8_t* pass_ws = ws + 256 + grads + lbytes;
+  GPL1_CUDA(cudaMemsetAsync(gerr, 0, sizeof(int), ctx->stream), "cudaMemsetAsync");
+  const long long nb = N / batch;
+  for (int s = 0; s < steps; ++s) {
+    const long long b0 = (s % nb) * batch;
+    const int r = lista_pass(ctx->encode, pass_ws, gerr, K, n, p, ldk, layers, W, true, theta, Y + b0 * ldy, ldy,
+                             batch, Xt + b0 * ldt, ldt, nullptr, 0, dW, dth, dloss + s, ctx->stream);
+    if (r != 0) return lista_status(ctx, r, gerr);
+    GPL1_CUDA(lista_adam_step(W, dW, adam_m, adam_v, static_cast<long long>(wcount), lr, t0 + s + 1, ctx->stream),
+              "adam");
+    GPL1_CUDA(lista_adam_step(theta, dth, adam_m + wcount, adam_v + wcount, layers, lr_theta, t0 + s + 1, ctx->stream),
+              "adam");
+  }
+  if (losses)
+    GPL1_CUDA(cudaMemcpyAsync(losses, dloss, static_cast<size_t>(steps) * 8, cudaMemcpyDeviceToHost, ctx->stream),
+              "cudaMemcpyAsync");
+  return lista_status(ctx, 0, gerr);
+}

@@ -3,13 +3,15 @@
 // Alg. GP, where many instances of eq. 2 share one K and the gradient and the
 // K-products of all of them become matrix products.
 //
-//   C (M x N, FP32) = A (M x Kd) * B (N x Kd)^T,  out[n * ldo + m] = scale * C[m][n]
+//   C (M x N, FP32) = A (M x Kd) * B (N x Kd)^T,
+//   out[n * ldo + m] = scale * C[m][n]   (transposed store), or
+//   out[m * ldo + n] = scale * C[m][n]   (row-major store)
 //
 // A and B are BF16, row-major with K contiguous (K-major).  A may be shorter
 // along K than B (Ka < Kd): its K coordinate wraps modulo Ka, so the split
 // vector operand [hi | mid | lo] of B multiplies the same A three times in one
-// accumulation.  The output is written transposed, so that each right-hand
-// side's vector is contiguous.
+// accumulation.  The transposed store makes each right-hand side's vector
+// contiguous; the row-major one keeps batch-major activations batch-major.
 //
 // One CTA per 128 x BN tile, 128 threads: thread 0 issues the TMA loads of a
 // 4-stage ring (128-byte swizzle), thread 32 issues the MMAs (128 x BN x 16
@@ -33,6 +35,7 @@ struct GemmArgs {
   float scale;
   int* err;
   long long timeout_ns;
+  int trans_out;
 };
 
 template <int BN>
@@ -132,10 +135,17 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn(const __grid_constant__ C
       float v[16];
       tc::ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0), v);
       if (m < g.M) {
+        if (g.trans_out) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int n = n0 + c0 + q;
-          if (n < g.N) g.out[static_cast<long long>(n) * g.ldo + m] = g.scale * v[q];
+          for (int q = 0; q < 16; ++q) {
+            const int n = n0 + c0 + q;
+            if (n < g.N) g.out[static_cast<long long>(n) * g.ldo + m] = g.scale * v[q];
+          }
+        } else {
+          float* row = g.out + static_cast<long long>(m) * g.ldo + n0 + c0;
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (n0 + c0 + q < g.N) row[q] = g.scale * v[q];
         }
       }
     }
@@ -180,11 +190,11 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const GemmAr
 
 int launch_gemm_bf16(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* A, int M, int Ka, long long lda,
                      const void* B, int N, int Kd, long long ldb, float* out, long long ldo, float scale, int* err,
-                     long long timeout_ns, int bn, cudaStream_t stream) {
+                     long long timeout_ns, int bn, cudaStream_t stream, int trans_out) {
   CUtensorMap ta, tb;
   if (encode_kmajor(enc, &ta, A, M, Ka, lda, kTcBM) != CUDA_SUCCESS) return -1;
   if (encode_kmajor(enc, &tb, B, N, Kd, ldb, bn) != CUDA_SUCCESS) return -1;
-  GemmArgs g{M, N, Kd, Ka, out, ldo, scale, err, timeout_ns};
+  GemmArgs g{M, N, Kd, Ka, out, ldo, scale, err, timeout_ns, trans_out};
   const cudaError_t e = bn == 256 ? launch_bn<256>(ta, tb, g, stream) : launch_bn<128>(ta, tb, g, stream);
   return static_cast<int>(e);
 }

@@ -23,13 +23,14 @@ cudaError_t launch_project(int dtype, const void* v, void* out, long long p, lon
                            long long stride, const double* rho, double* tau, cudaStream_t stream);
 long long project_max_p(int dtype);
 
-// BF16 tensor-core GEMM (gemm_tc.cu): out[n * ldo + m] = scale * sum_k A[m][k % Ka] B[n][k],
+// BF16 tensor-core GEMM (gemm_tc.cu): C[m][n] = scale * sum_k A[m][k % Ka] B[n][k],
+// stored out[n * ldo + m] (trans_out = 1) or out[m * ldo + n] (trans_out = 0);
 // A M x Ka (row stride lda), B N x Kd (row stride ldb), Kd a multiple of 64, Ka of 64.
 // bn: 128 or 256 (tile width along N).  Returns a cudaError_t, or -1 if a tensor map
 // could not be encoded.
 int launch_gemm_bf16(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* A, int M, int Ka, long long lda,
                      const void* B, int N, int Kd, long long ldb, float* out, long long ldo, float scale, int* err,
-                     long long timeout_ns, int bn, cudaStream_t stream);
+                     long long timeout_ns, int bn, cudaStream_t stream, int trans_out = 1);
 
 }  // namespace gpl1
 
@@ -47,4 +48,15 @@ cudaError_t launch_mr_phase_l(const float* KDX, const void* Kt, const float* Y, 
                               void* states, const SolveParams& prm, gpl1_result* res, int* done_count,
                               cudaStream_t s);
 cudaError_t launch_transpose_bf16(const void* K, long long ldk, void* Kt, int n, int p, cudaStream_t s);
+}  // namespace gpl1
+
+namespace gpl1 {
+// Learned warm start (lista.cu).
+size_t lista_ws_bytes(int L, long long n, long long p, long long B);
+int lista_pass(PFN_cuTensorMapEncodeTiled_v12000 enc, uint8_t* ws, int* gerr, const void* K, long long n, long long p,
+               long long ldk, int L, const float* W, bool convert_w, const float* theta, const float* Y,
+               long long ldy, long long B, const float* Xt, long long ldt, float* Xout, long long ldx, float* dW,
+               float* dtheta, double* loss_out, cudaStream_t s);
+cudaError_t lista_adam_step(float* w, const float* g, float* m, float* v, long long count, float lr, int t,
+                            cudaStream_t s);
 }  // namespace gpl1

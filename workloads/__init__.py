@@ -176,8 +176,9 @@ def ragged_instance(i: int, n: int, *, dtype: int = DT_BF16, seed: int = SEED_BA
 
 
 def shared_k(n: int = 2048, p: int = 8192, nrhs: int = 1024, k: int = 102, *,
-             dtype: int = DT_BF16, seed: int = SEED_BASE + 4, sigma: float = 0.01):
-    """One K shared by nrhs right-hand sides, each from its own +-1 k-sparse signal.
+             dtype: int = DT_BF16, seed: int = SEED_BASE + 4, sigma: float = 0.01, law: str = "pm1"):
+    """One K shared by nrhs right-hand sides, each from its own k-sparse signal
+    (+-1 entries, or N(0,1) entries for law="gauss").
 
     Returns (K stored n x ldk, ldk, Y float32 nrhs x n, rho float64 nrhs, X_true nrhs x p).
     """
@@ -186,7 +187,15 @@ def shared_k(n: int = 2048, p: int = 8192, nrhs: int = 1024, k: int = 102, *,
     ldk = padded_ld(p, dtype)
     Ks = _store(K64, dtype, ldk)
     Kw = bf16_bits_to_f64(Ks[:, :p]) if dtype == DT_BF16 else np.asarray(Ks[:, :p], np.float64)
-    X = np.stack([_sparse_signal(rng, p, k, "pm1") for _ in range(nrhs)])
+    X = np.stack([_sparse_signal(rng, p, k, law) for _ in range(nrhs)])
     Y = (X @ Kw.T + sigma * rng.standard_normal((nrhs, n))).astype(np.float32)
     rho = np.abs(X).sum(axis=1)
     return Ks, ldk, Y, rho, X
+
+
+def warm_start_data(n: int = 1024, p: int = 4096, count: int = 100_000, k: int = 50, *,
+                    seed: int = SEED_BASE + 5, sigma: float = 0.01):
+    """Learned-warm-start recipe: K n x p N(0, 1/n) (BF16), `count` right-hand sides
+    from k-sparse Bernoulli-Gaussian signals (N(0,1) values), noise sigma,
+    rho = ||x_true||_1 per sample.  Returns (K, ldk, Y, rho, X_true)."""
+    return shared_k(n, p, count, k, dtype=DT_BF16, seed=seed, sigma=sigma, law="gauss")
