@@ -195,8 +195,9 @@ gpl1_status gpl1_gemm_bf16(gpl1_ctx* ctx, const void* A, long long M, long long 
  * tensor-core matrix products (gpl1_gemm_bf16, FP32 vectors carried as three
  * BF16 terms), the steplength, projection and line search per instance.
  *   Y: device, nrhs rows of n floats (row stride ldy); X: device, nrhs rows of
- *   p floats (row stride ldx), the solutions on exit (x0 = 0: prm->x0_is_zero
- *   must be set).  rho, f_star: host arrays of nrhs doubles (f_star may be
+ *   p floats (row stride ldx): x0 on entry (ignored when prm->x0_is_zero is
+ *   set; projected onto its ball first if it lies outside), the solutions on
+ *   exit.  rho, f_star: host arrays of nrhs doubles (f_star may be
  *   NULL; otherwise it enables GPL1_STOP_ON_REL_GAP per instance).  res: host
  *   array of nrhs results (kernel_ms = the whole solve).  n and p must be
  *   multiples of 64, p <= 16800.  The call synchronises the context stream. */

@@ -290,14 +290,18 @@ class Context:
 
     def solve_shared_k(self, K, Y, rho, p=None, f_star=None, params: Params | None = None, X=None):
         """gpl1_solve_shared_k: instances sharing the BF16 K (n, ldk) with right-hand sides
-        Y (nrhs, n) float32 and radii rho (nrhs); returns (X (nrhs, p) float32, [Result])."""
+        Y (nrhs, n) float32 and radii rho (nrhs); X (nrhs, p) float32 holds x0 when given
+        (else x0 = 0); returns (X, [Result])."""
         import torch
         n, ldk = K.shape
         nrhs = Y.shape[0]
         p = ldk if p is None else int(p)
-        X = torch.empty(nrhs, p, dtype=torch.float32, device=K.device) if X is None else X
         prm = Params.from_buffer_copy(params_default() if params is None else params)
-        prm.x0_is_zero = 1
+        if X is None:
+            X = torch.empty(nrhs, p, dtype=torch.float32, device=K.device)
+            prm.x0_is_zero = 1
+        else:
+            prm.x0_is_zero = 0
         rho_h = (ctypes.c_double * nrhs)(*[float(r) for r in rho])
         fs_h = None if f_star is None else (ctypes.c_double * nrhs)(*[float(f) for f in f_star])
         res = (Result * nrhs)()

@@ -620,7 +620,6 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
   if (ldy < n || ldx < p) return fail(ctx, GPL1_ERR_INVALID_ARG, "need ldy >= n and ldx >= p");
   for (int b = 0; b < nrhs; ++b)
     if (!(rho[b] > 0) || !std::isfinite(rho[b])) return fail(ctx, GPL1_ERR_INVALID_ARG, "rho[%d] must be > 0", b);
-  if (!prm->x0_is_zero) return fail(ctx, GPL1_ERR_UNSUPPORTED, "the shared-K form starts from x0 = 0");
   GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
   if (!ctx->encode) {
     cudaDriverEntryPointQueryResult q;
@@ -669,10 +668,21 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
   }
   GPL1_CUDA(cudaEventRecord(ctx->ev[0], s), "cudaEventRecord");
   GPL1_CUDA(launch_transpose_bf16(K, ldk, Kt, static_cast<int>(n), static_cast<int>(p), s), "transpose");
-  GPL1_CUDA(launch_mr_init(Y, ldy, X, ldx, Rs, static_cast<int>(n), static_cast<int>(p), rho_d,
-                           f_star ? fs_d : nullptr, states, sp, nrhs, s),
-            "init");
   const long long tmo = prm->timeout_ns;
+  if (prm->x0_is_zero) {
+    GPL1_CUDA(launch_mr_init(Y, ldy, X, ldx, Rs, static_cast<int>(n), static_cast<int>(p), rho_d,
+                             f_star ? fs_d : nullptr, states, sp, nrhs, s),
+              "init");
+  } else {   // x0 given: into the balls, K x0 on the tensor cores, then r0 and f0
+    GPL1_CUDA(launch_mr_setup_x0(X, ldx, DXs, static_cast<int>(p), nrhs, rho_d, s), "setup x0");
+    const int e0 = launch_gemm_bf16(ctx->encode, K, static_cast<int>(n), static_cast<int>(p), ldk, DXs, 2 * nrhs,
+                                    static_cast<int>(3 * p), 3 * p, KDX, n, 1.f, gerr, tmo,
+                                    ((n + 127) / 128) * ((2LL * nrhs + 255) / 256) < ctx->num_sms ? 128 : 256, s);
+    if (e0) return e0 == -1 ? fail(ctx, GPL1_ERR_CUDA, "tensor map") : cuda_fail(ctx, static_cast<cudaError_t>(e0), "K x0");
+    GPL1_CUDA(launch_mr_setup_r(KDX, Y, ldy, Rs, static_cast<int>(n), nrhs, rho_d, f_star ? fs_d : nullptr, states,
+                                sp, s),
+              "setup r0");
+  }
   auto bn_for = [&](long long M, long long Nc) {
     return ((M + 127) / 128) * ((Nc + 255) / 256) < ctx->num_sms ? 128 : 256;
   };

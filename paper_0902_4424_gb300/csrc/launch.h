@@ -48,6 +48,11 @@ cudaError_t launch_mr_phase_l(const float* KDX, const void* Kt, const float* Y, 
                               void* states, const SolveParams& prm, gpl1_result* res, int* done_count,
                               cudaStream_t s);
 cudaError_t launch_transpose_bf16(const void* K, long long ldk, void* Kt, int n, int p, cudaStream_t s);
+cudaError_t launch_mr_setup_x0(float* X, long long ldx, uint16_t* DXs, int p, int nrhs, const double* rho,
+                               cudaStream_t s);
+cudaError_t launch_mr_setup_r(const float* KDX, const float* Y, long long ldy, uint16_t* Rs, int n, int nrhs,
+                              const double* rho, const double* fstar, void* states, const SolveParams& prm,
+                              cudaStream_t s);
 }  // namespace gpl1
 
 namespace gpl1 {

@@ -138,6 +138,91 @@ __global__ void __launch_bounds__(kConsumers) mr_init(const float* Y, long long 
   }
 }
 
+// Given x0 (rows of X): project it onto its ball where it lies outside (Alg.
+// GP starts in Omega), then lay out its BF16 terms (and d = 0) for K [D; X]^T.
+__global__ void __launch_bounds__(kConsumers) mr_setup_x0(float* X, long long ldx, uint16_t* DXs, int p, int nrhs,
+                                                          const double* rho) {
+  const int b = blockIdx.x, tid = threadIdx.x;
+  extern __shared__ uint8_t mr_raw[];
+  MrSmem& sm = *reinterpret_cast<MrSmem*>(mr_raw);
+  float* const xs = sm.xs;
+  float* x = X + b * ldx;
+  const int neu = (p + kConsumers - 1) / kConsumers;
+  for (int e = 0; e < neu; ++e) {
+    const int j = tid + e * kConsumers;
+    xs[e * kConsumers + tid] = j < p ? x[j] : 0.f;
+  }
+  if (tid == 0) {
+    const F2 rp = f2_of(rho[b]);
+    sm.sc.tp[0] = rp.hi;
+    sm.sc.tp[1] = rp.lo;
+  }
+  consumer_sync();
+  const F2 rho_p{sm.sc.tp[0], sm.sc.tp[1]};
+  consumer_sync();
+  const SmemAcc<float, kMrVmax> acc{xs, neu};
+  const TauResult t = block_l1_tau_fixed_point<float>(acc, rho[b], rho_p, 0.f, sm.ps, sm.sc);
+  const TauPair tp{t.th, t.tl};
+  uint16_t* dd_s = DXs + static_cast<long long>(b) * 3 * p;
+  uint16_t* xx_s = DXs + static_cast<long long>(nrhs + b) * 3 * p;
+  for (int e = 0; e < neu; ++e) {
+    const int j = tid + e * kConsumers;
+    if (j >= p) break;
+    const float v = xs[e * kConsumers + tid];
+    const float a = fabsf(v);
+    const float xj = t.inside ? v : (tp.below(a) ? 0.f : copysignf((a - tp.hi) - tp.lo, v));
+    x[j] = xj;
+    uint16_t h, m, l;
+    split3(xj, h, m, l);
+    xx_s[j] = h;
+    xx_s[p + j] = m;
+    xx_s[2 * p + j] = l;
+    dd_s[j] = dd_s[p + j] = dd_s[2 * p + j] = 0;
+  }
+}
+
+// Initial state from r0 = K x0 - y (K x0 from the tensor-core product).
+__global__ void __launch_bounds__(kConsumers) mr_setup_r(const float* KDX, const float* Y, long long ldy,
+                                                         uint16_t* Rs, int n, int nrhs, const double* rho,
+                                                         const double* fstar, MrState* st, SolveParams prm) {
+  const int b = blockIdx.x, tid = threadIdx.x;
+  __shared__ Scratch sc;
+  const float* kx = KDX + static_cast<long long>(nrhs + b) * n;
+  const float* y = Y + b * ldy;
+  uint16_t* rs = Rs + static_cast<long long>(b) * 3 * n;
+  F2 ff{0.f, 0.f}, yy{0.f, 0.f};
+  for (int i = tid; i < n; i += kConsumers) {
+    const F2 r = two_sum(kx[i], -y[i]);
+    ff = f2_fma(ff, r.hi, r.hi + 2.f * r.lo);
+    yy = f2_fma(yy, y[i], y[i]);
+    uint16_t h, m, l;
+    split3(r.hi + r.lo, h, m, l);
+    rs[i] = h;
+    rs[n + i] = m;
+    rs[2 * n + i] = l;
+  }
+  F2 v[2] = {ff, yy};
+  unsigned dummy = 0;
+  lead_reduce<2>(v, dummy, sc);
+  if (tid == 0) {
+    MrState s;
+    memset(&s, 0, sizeof s);
+    s.ss.tau_ss = static_cast<float>(prm.tau1);
+    const double f0 = as_double(v[0]), y2 = as_double(v[1]);
+    s.f_cur = f0;
+    for (int q = 0; q < kMaxM; ++q) s.fhist[q] = f0;
+    s.rho = rho[b];
+    const F2 rp = f2_of(rho[b]);
+    s.rho_hi = rp.hi;
+    s.rho_lo = rp.lo;
+    s.f_star = fstar ? fstar[b] : -1.0;
+    s.gap_den = fmax(s.f_star, prm.tol * y2);
+    s.xscale = 1.f;
+    s.stop = GPL1_STOP_MAX_ITER;
+    st[b] = s;
+  }
+}
+
 // d_j from the float pair of alpha (hi only here) and tau, as in pass B of the
 // single solve: the active form never subtracts x from a number of its size.
 __device__ __forceinline__ float mr_dir(float x, float g, float ah, float th, float tl, int inside) {
@@ -524,6 +609,21 @@ __global__ void transpose_bf16(const uint16_t* K, long long ldk, uint16_t* Kt, i
 }
 
 size_t mr_phase_p_smem() { return sizeof(MrSmem); }
+
+cudaError_t launch_mr_setup_x0(float* X, long long ldx, uint16_t* DXs, int p, int nrhs, const double* rho,
+                               cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(mr_setup_x0, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sizeof(MrSmem)));
+  if (e != cudaSuccess) return e;
+  mr_setup_x0<<<nrhs, kConsumers, sizeof(MrSmem), s>>>(X, ldx, DXs, p, nrhs, rho);
+  return cudaGetLastError();
+}
+cudaError_t launch_mr_setup_r(const float* KDX, const float* Y, long long ldy, uint16_t* Rs, int n, int nrhs,
+                              const double* rho, const double* fstar, void* states, const SolveParams& prm,
+                              cudaStream_t s) {
+  mr_setup_r<<<nrhs, kConsumers, 0, s>>>(KDX, Y, ldy, Rs, n, nrhs, rho, fstar, static_cast<MrState*>(states), prm);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mr_init(const float* Y, long long ldy, float* X, long long ldx, uint16_t* Rs, int n, int p,
                            const double* rho, const double* fstar, void* states, const SolveParams& prm, int nrhs,

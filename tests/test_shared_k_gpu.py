@@ -68,3 +68,22 @@ def test_shared_k_rejects_unsupported_shapes(gpu_ctx):
     with pytest.raises(pkg.Gpl1Error) as e:
         gpu_ctx.solve_shared_k(K, Y, [1.0, 1.0])
     assert e.value.status == 7
+
+
+def test_shared_k_from_given_x0(gpu_ctx):
+    """x0 given (here infeasible: 3 x_true lies outside the ball of radius ||x_true||_1):
+    projected first, then solved to the same oracle gap."""
+    n, p, nrhs, k = 256, 1024, 8, 12
+    Ks, ldk, Y, rho, probs = instances(n, p, nrhs, k, seed=23)
+    fstar = np.array([oracle.reference_solve(pr)[1].f for pr in probs])
+    K = torch.from_numpy(Ks.view(np.int16)).to(DEV)
+    Yd = torch.from_numpy(Y).to(DEV)
+    X0 = torch.from_numpy(np.stack([3.0 * pr.x_true for pr in probs]).astype(np.float32)).to(DEV)
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, max_iter=3000)
+    X, res = gpu_ctx.solve_shared_k(K, Yd, rho, p=p, f_star=fstar, params=prm, X=X0)
+    torch.cuda.synchronize()
+    Xh = X.double().cpu().numpy()
+    for b in range(nrhs):
+        assert res[b].status == 0, (b, res[b].as_dict())
+        assert (oracle.objective(probs[b], Xh[b]) - fstar[b]) / fstar[b] <= 1e-6
+        assert np.abs(Xh[b]).sum() <= rho[b] * (1 + 1e-6)
