@@ -191,6 +191,16 @@ def whole_job_rate(world: int, steps: int, max_total_ms: float) -> float:
     return world * steps / (max_total_ms / 1e3)
 
 
+def objective_f64(prob, x) -> float:
+    """f(x) = ||K x - y||^2 in FP64 on the stored K (numpy; a check of the returned
+    x against the stored optimum, outside every timed region)."""
+    import workloads as W
+    K = prob.K[:, :prob.p]
+    K64 = W.bf16_bits_to_f64(K) if prob.dtype == W.DT_BF16 else np.asarray(K, np.float64)
+    r = K64 @ np.asarray(x, np.float64) - np.asarray(prob.y, np.float64)
+    return float(r @ r)
+
+
 # ------------------------------------------------- batched ragged form (c3a)
 def run_batched(count, steps, dev):
     """Solves/s of `count` instances of the ragged recipe (n in [128, 2048], p = 4n,
@@ -200,7 +210,6 @@ def run_batched(count, steps, dev):
     (tests/golden/c3a_fstar.json, written by tests/golden/make_golden.py)."""
     import torch
 
-    import oracle
     import paper_0902_4424_gb300 as pkg
     import workloads as W
     sizes = W.ragged_sizes(512)[:count]
@@ -247,7 +256,7 @@ def run_batched(count, steps, dev):
     # untimed: the oracle's optimum on a few instances, against the batched x
     ctx.solve_batched(descs, pkg.BF16, prm)
     torch.cuda.synchronize()
-    gaps = [(oracle.objective(probs[q], keep[q][2].double().cpu().numpy()) - fstars[q]) / max(fstars[q], 1e-300)
+    gaps = [(objective_f64(probs[q], keep[q][2].double().cpu().numpy()) - fstars[q]) / max(fstars[q], 1e-300)
             for q in range(count)]
     peak, _ = peaks()
     mean_ms = statistics.mean(ms)
@@ -271,7 +280,6 @@ def run_shared_k(nrhs, dev, verify=16, plain=8):
     instance (tests/golden/c3b_fstar.json); x is checked by the oracle on a sample."""
     import torch
 
-    import oracle
     import paper_0902_4424_gb300 as pkg
     import workloads as W
     with open(os.path.join(ROOT, "tests", "golden", "c3b_fstar.json")) as fh:
@@ -297,7 +305,7 @@ def run_shared_k(nrhs, dev, verify=16, plain=8):
     Xh = X.double().cpu().numpy()
     probs = [W.Problem(Ks, n, p, ldk, W.DT_BF16, Y[q].copy(), float(rho[q]), Xt[q], f"c3b_{q}") for q in range(nrhs)]
     idx = np.linspace(0, nrhs - 1, min(verify, nrhs)).astype(int)
-    gaps = [(oracle.objective(probs[q], Xh[q]) - fstars[q]) / fstars[q] for q in idx]
+    gaps = [(objective_f64(probs[q], Xh[q]) - fstars[q]) / fstars[q] for q in idx]
     # the plain form on a sample: each instance its own cooperative solve of K
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -328,6 +336,92 @@ def run_shared_k(nrhs, dev, verify=16, plain=8):
            "note": "executed GEMM work incl. the 3-term BF16 split of the vector operand; all iterations of the call"}
     ctx.close()
     return out
+
+
+# ------------------------------------------------ learned warm start (c4)
+def run_warm_start(dev, steps=600, batch=256):
+    """The learned warm start on K 1024 x 4096 (BF16): training targets are the
+    solver's own solutions of the training samples (shared-K form), the network
+    (6 layers, W_l initialised to K^T / ||K||^2, theta_l to the median lambda /
+    ||K||^2) is trained with Adam on the GPU, and the test samples are solved to
+    relative gap 1e-6 (kernel stop 5e-7, stored oracle optima) from x0 = 0 (cold)
+    and from the projected network output (warm, inference included)."""
+    import torch
+
+    import paper_0902_4424_gb300 as pkg
+    import workloads as W
+    with open(os.path.join(ROOT, "tests", "golden", "c4_fstar.json")) as fh:
+        gold = json.load(fh)
+    Ks, ldk, Y, rho, Xt, ntr = W.warm_start_split()
+    n, p = Ks.shape[0], Xt.shape[1]
+    nte = Y.shape[0] - ntr
+    fstars = gold["f_star"]
+    K = torch.from_numpy(Ks.view(np.int16)).to(dev)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y)).to(dev)
+    ctx = pkg.Context(dev.index or 0)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+    # training targets: solutions of eq. 2 for the training samples (shared-K form)
+    a, b = ev(), ev()
+    a.record(stream)
+    targets, lams = [], []
+    for c0 in range(0, ntr, 4096):
+        Xs, res = ctx.solve_shared_k(K, Yd[c0:c0 + 4096], rho[c0:c0 + 4096], p=p,
+                                     params=pkg.params_default(stop_rule=0, max_iter=120))
+        targets.append(Xs)
+        lams += [r.lambda_ for r in res]
+    Xtr = torch.cat(targets)
+    b.record(stream)
+    b.synchronize()
+    target_ms = a.elapsed_time(b)
+    # network: W_l = K^T / L, theta_l = median(lambda) / L, L = ||K||_2^2
+    K64 = W.bf16_bits_to_f64(Ks[:, :p])
+    Lk = float(np.linalg.norm(K64, 2) ** 2)
+    layers = 6
+    Wd = (torch.from_numpy((K64.T / Lk).astype(np.float32)).to(dev)).unsqueeze(0).repeat(layers, 1, 1).contiguous()
+    thd = torch.full((layers,), float(np.median(lams)) / Lk, dtype=torch.float32, device=dev)
+    m = torch.zeros(layers * p * n + layers, dtype=torch.float32, device=dev)
+    v = torch.zeros_like(m)
+    a, b = ev(), ev()
+    a.record(stream)
+    losses = ctx.lista_train(K, Wd, thd, m, v, Yd[:ntr], Xtr, batch=batch, steps=steps, lr=1e-4, lr_theta=1e-4)
+    b.record(stream)
+    b.synchronize()
+    train_ms = a.elapsed_time(b)
+    # test: cold and warm solves of the test samples
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=0.5 * TOL, max_iter=5000)
+    Yte = Yd[ntr:]
+    ctx.solve_shared_k(K, Yte, rho[ntr:], p=p, f_star=fstars, params=prm)   # warm-up
+    a, b = ev(), ev()
+    a.record(stream)
+    Xc, rc = ctx.solve_shared_k(K, Yte, rho[ntr:], p=p, f_star=fstars, params=prm)
+    b.record(stream)
+    b.synchronize()
+    cold_ms = a.elapsed_time(b)
+    a, b = ev(), ev()
+    a.record(stream)
+    X0 = ctx.lista_forward(K, Wd, thd, Yte)
+    Xw, rw = ctx.solve_shared_k(K, Yte, rho[ntr:], p=p, f_star=fstars, params=prm, X=X0)
+    b.record(stream)
+    b.synchronize()
+    warm_ms = a.elapsed_time(b)
+    probs = [W.Problem(Ks, n, p, ldk, W.DT_BF16, Y[ntr + q].copy(), float(rho[ntr + q]), Xt[ntr + q], "c4")
+             for q in range(nte)]
+    Xwh = Xw.double().cpu().numpy()
+    idx = np.linspace(0, nte - 1, 16).astype(int)
+    gaps = [(objective_f64(probs[q], Xwh[q]) - fstars[q]) / fstars[q] for q in idx]
+    ctx.close()
+    return {"workload": f"c4_warmstart{n}x{p}_bf16", "train_samples": ntr, "test_samples": nte,
+            "layers": layers, "train_steps": steps, "batch": batch, "train_ms": train_ms,
+            "target_solve_ms": target_ms, "loss_first": float(np.mean(losses[:8])),
+            "loss_last": float(np.mean(losses[-8:])),
+            "cold_solves_per_s": nte / (cold_ms / 1e3), "warm_solves_per_s": nte / (warm_ms / 1e3),
+            "cold_iters_mean": statistics.mean(r.iters for r in rc),
+            "warm_iters_mean": statistics.mean(r.iters for r in rw),
+            "cold_ok": sum(r.status == 0 for r in rc), "warm_ok": sum(r.status == 0 for r in rw),
+            "warm_verified_max_rel_gap": max(gaps), "verified_instances": len(gaps),
+            "stop": f"kernel stop rel_gap<={0.5 * TOL:g} vs oracle f* per test sample",
+            "note": "warm time includes the network's inference; both solved in one shared-K call"}
 
 
 # -------------------------------------------------------------- GPU path
@@ -393,8 +487,7 @@ def run_ours(args, rank, world, local_rank):
     value = whole_job_rate(world, args.steps, total_ms_max)
 
     # ---- check the objective actually reached (FP64 on the host, untimed)
-    import oracle
-    f_gpu = oracle.objective(prob, x.double().cpu().numpy())
+    f_gpu = objective_f64(prob, x.double().cpu().numpy())
     verified_gap = (f_gpu - fstar) / fstar
 
     # ---- end to end through the public API with host buffers
@@ -467,6 +560,8 @@ def run_ours(args, rank, world, local_rank):
         line["batched"] = run_batched(args.batched_sample, 3, dev)
     if args.shared_k > 0 and os.path.exists(os.path.join(ROOT, "tests", "golden", "c3b_fstar.json")):
         line["shared_k"] = run_shared_k(args.shared_k, dev)
+    if args.warm_start and os.path.exists(os.path.join(ROOT, "tests", "golden", "c4_fstar.json")):
+        line["warm_start"] = run_warm_start(dev)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -495,6 +590,7 @@ def main():
                     help="also time this many ragged instances batched vs plain (0: skip)")
     ap.add_argument("--shared-k", type=int, default=1024,
                     help="also time this many right-hand sides on one shared K (0: skip)")
+    ap.add_argument("--warm-start", type=int, default=1, help="also measure the learned warm start (0: skip)")
     ap.add_argument("--workload", choices=["c1", "c3a"], default="c1",
                     help="c3a: only the batched ragged form, all 512 instances")
     args = ap.parse_args()

@@ -7,6 +7,7 @@ no decrease of f for 30 iterations).  Nothing here touches the CUDA path.
     python tests/golden/make_golden.py [c0 c1 c2 ...]
     python tests/golden/make_golden.py c3a      # the ragged batch: c3a_fstar.json
     python tests/golden/make_golden.py c3b      # the shared-K right-hand sides: c3b_fstar.json
+    python tests/golden/make_golden.py c4       # the warm-start test samples: c4_fstar.json
 """
 import json
 import os
@@ -77,8 +78,28 @@ def main_c3b(nrhs=1024):
                    "solver": "oracle.floor_solve"}, fh, indent=0)
 
 
+def main_c4():
+    """tests/golden/c4_fstar.json: f* of the learned-warm-start workload's test
+    samples (the oracle's floor solve of each)."""
+    out = os.path.join(os.path.dirname(OUT), "c4_fstar.json")
+    t = time.time()
+    Ks, ldk, Y, rho, X, ntr = W.warm_start_split()
+    n, p = Ks.shape[0], X.shape[1]
+    fs = []
+    for q in range(ntr, Y.shape[0]):
+        prob = W.Problem(Ks, n, p, ldk, W.DT_BF16, Y[q].copy(), float(rho[q]), X[q], f"c4_{q}")
+        fs.append(oracle.floor_solve(prob)[1].f)
+    print(len(fs), f"{time.time() - t:.0f}s", flush=True)
+    with open(out, "w") as fh:
+        json.dump({"workload": "c4_warmstart1024x4096_bf16", "first_test_row": ntr, "f_star": fs,
+                   "solver": "oracle.floor_solve"}, fh, indent=0)
+
+
 if __name__ == "__main__":
     args = sys.argv[1:]
+    if args == ["c4"]:
+        main_c4()
+        sys.exit(0)
     if args == ["c3a"]:
         main_c3a()
     elif args == ["c3b"]:

@@ -199,3 +199,14 @@ def warm_start_data(n: int = 1024, p: int = 4096, count: int = 100_000, k: int =
     from k-sparse Bernoulli-Gaussian signals (N(0,1) values), noise sigma,
     rho = ||x_true||_1 per sample.  Returns (K, ldk, Y, rho, X_true)."""
     return shared_k(n, p, count, k, dtype=DT_BF16, seed=seed, sigma=sigma, law="gauss")
+
+
+# The learned-warm-start workload as measured: training and test samples of one
+# warm_start_data draw (the test samples are its last rows).
+WARM_TRAIN, WARM_TEST = 16384, 256
+
+
+def warm_start_split():
+    """(K, ldk, Y, rho, X_true, ntrain): the measured warm-start workload, K 1024 x 4096."""
+    Ks, ldk, Y, rho, X = warm_start_data(1024, 4096, WARM_TRAIN + WARM_TEST, 50)
+    return Ks, ldk, Y, rho, X, WARM_TRAIN
