@@ -686,7 +686,6 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
   auto bn_for = [&](long long M, long long Nc) {
     return ((M + 127) / 128) * ((Nc + 255) / 256) < ctx->num_sms ? 128 : 256;
   };
-  int iters_run = 0;
   for (int k = 0; k < prm->max_iter; ++k) {
     float* Gc = G[k & 1];
     float* Gp = G[(k + 1) & 1];
@@ -700,7 +699,6 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
     GPL1_CUDA(launch_mr_phase_l(KDX, Kt, Y, ldy, X, ldx, D, Rs, static_cast<int>(n), static_cast<int>(p), nrhs, k,
                                 states, sp, rdev, done_count, s),
               "phase L");
-    iters_run = k + 1;
     if ((k & 3) == 3 || k + 1 == prm->max_iter) {
       int hd[2] = {0, 0};
       GPL1_CUDA(cudaMemcpyAsync(hd, ws, 2 * sizeof(int), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
@@ -711,7 +709,6 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
       if (ge) return fail(ctx, static_cast<gpl1_status>(ge), "a bounded wait in a GEMM ran out");
     }
   }
-  (void)iters_run;
   GPL1_CUDA(cudaEventRecord(ctx->ev[1], s), "cudaEventRecord");
   GPL1_CUDA(cudaMemcpyAsync(res, rdev, N * sizeof(gpl1_result), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(res)");
   GPL1_CUDA(cudaStreamSynchronize(s), "shared-K solve");

@@ -415,8 +415,11 @@ struct Consumer {
         red_release_add(a.bar, 1u);
         const unsigned target =
             epoch * static_cast<unsigned>(G) + ((a.prm.debug & kDebugUnreachableBarrier) ? 1u : 0u);
+        // poll with relaxed loads (one round trip each; the fence after the
+        // loop orders what follows); the error flag and the clock every 16th
         const uint64_t t0 = globaltimer();
-        while (ld_acquire(a.bar) < target) {
+        for (unsigned poll = 0; ld_relaxed(a.bar) < target; ++poll) {
+          if ((poll & 15u) != 15u) continue;
           if (ld_volatile(a.err)) break;
           if (globaltimer() - t0 > static_cast<uint64_t>(a.prm.timeout_ns)) {
             atomicCAS(a.err, 0, GPL1_ERR_TIMEOUT);
