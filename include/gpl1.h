@@ -189,18 +189,45 @@ gpl1_status gpl1_gemm_bf16(gpl1_ctx* ctx, const void* A, long long M, long long 
                            const void* B, long long N, long long Kd, long long ldb, float* out,
                            long long ldo, float scale);
 
+/* gpl1_gemm_bf16 with an explicit kernel configuration and a split of the
+ * contraction.  config: 0 = 128 x 128 output tiles, 4-stage load ring (one CTA
+ * per SM); 1 = 128 x 256 tiles, 4 stages; 2 = 128 x 128, 3 stages (two CTAs per
+ * SM); 3 = 128 x 128, 6 stages.  splits in [1, Kd / 64]: part z sums the
+ * 64-wide k-blocks [z KB / splits, (z+1) KB / splits) (KB = Kd / 64) and is
+ * written, in the layout of gpl1_gemm_bf16, to out + z * split_stride (floats,
+ * split_stride >= N * ldo when splits > 1); the parts add up to the product.
+ * The shared-K solve uses this to fill the GPU when M x N has few tiles.
+ * GPL1_ERR_INVALID_ARG for a config or split out of range. */
+gpl1_status gpl1_gemm_bf16_ex(gpl1_ctx* ctx, const void* A, long long M, long long Ka, long long lda,
+                              const void* B, long long N, long long Kd, long long ldb, float* out,
+                              long long ldo, float scale, int config, int splits,
+                              long long split_stride);
+
+/* The autotuner's choices.  gpl1_solve_shared_k times every configuration and
+ * admissible split of its two products on their operands the first time it
+ * meets a shape, adds the cost of summing the extra partials, and keeps the
+ * fastest per context.  Returns the number of tuned shapes (-1 for a NULL
+ * ctx); for 0 <= index < that number it also writes shape[5] = {M, N, Kd, Ka,
+ * max_splits}, the configuration, the split and the tuned time per product
+ * (ms).  Any output pointer may be NULL. */
+int gpl1_gemm_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* config, int* splits,
+                    float* ms);
+
 /* Solve nrhs instances of eq. 2 that share one K (GPL1_BF16, n x p, row
  * stride ldk) and differ in y and rho, with Alg. GP + SS per instance: the
- * gradients 2 K^T r and the products K d, K x of all instances are formed as
- * tensor-core matrix products (gpl1_gemm_bf16, FP32 vectors carried as three
- * BF16 terms), the steplength, projection and line search per instance.
+ * gradients 2 K^T r and the products K d of all instances are formed as
+ * tensor-core matrix products (gpl1_gemm_bf16_ex with autotuned configuration
+ * and split, FP32 vectors carried as three BF16 terms), r is carried and
+ * updated by lam K d (near the stop K x is summed exactly over the support of
+ * x instead), the steplength, projection and line search run per instance.
  *   Y: device, nrhs rows of n floats (row stride ldy); X: device, nrhs rows of
  *   p floats (row stride ldx): x0 on entry (ignored when prm->x0_is_zero is
  *   set; projected onto its ball first if it lies outside), the solutions on
  *   exit.  rho, f_star: host arrays of nrhs doubles (f_star may be
  *   NULL; otherwise it enables GPL1_STOP_ON_REL_GAP per instance).  res: host
  *   array of nrhs results (kernel_ms = the whole solve).  n and p must be
- *   multiples of 64, p <= 16800.  The call synchronises the context stream. */
+ *   multiples of 64, n <= 4320, p <= 16800 (GPL1_ERR_UNSUPPORTED otherwise).
+ *   The call synchronises the context stream. */
 gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
                                 const float* Y, long long ldy, const double* rho, const double* f_star,
                                 float* X, long long ldx, int nrhs, const gpl1_params* prm,

@@ -30,7 +30,8 @@ ALGORITHMIC = (0, 3, 4, 5, 6)
 
 EXPORTS = ["gpl1_create", "gpl1_destroy", "gpl1_set_stream", "gpl1_last_error", "gpl1_params_default",
            "gpl1_project", "gpl1_solve", "gpl1_solve_batched", "gpl1_solve_noalloc", "gpl1_gemm_bf16",
-           "gpl1_solve_shared_k", "gpl1_lista_forward", "gpl1_lista_grad", "gpl1_lista_train"]
+           "gpl1_gemm_bf16_ex", "gpl1_gemm_tuned", "gpl1_solve_shared_k", "gpl1_lista_forward",
+           "gpl1_lista_grad", "gpl1_lista_train"]
 
 
 class Gpl1Error(RuntimeError):
@@ -94,6 +95,11 @@ def lib():
         L.gpl1_gemm_bf16.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_float]
+        L.gpl1_gemm_bf16_ex.argtypes = L.gpl1_gemm_bf16.argtypes + [ctypes.c_int, ctypes.c_int, ctypes.c_longlong]
+        L.gpl1_gemm_tuned.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_float)]
+        L.gpl1_gemm_tuned.restype = ctypes.c_int
         L.gpl1_solve_shared_k.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
                                           ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
@@ -208,6 +214,34 @@ class Context:
                                   ctypes.c_void_p(B.data_ptr()), N, Kd, B.stride(0),
                                   ctypes.c_void_p(out.data_ptr()), out.stride(0), float(scale))
         self._check(st)
+        return out
+
+    def gemm_bf16_ex(self, A, B, config, splits, Kd=None, scale=1.0):
+        """gpl1_gemm_bf16_ex: the same product with kernel configuration `config` and the
+        contraction split into `splits` parts; returns the parts, (splits, N, M) FP32."""
+        import torch
+        M, Ka = A.shape
+        N, Kb = B.shape
+        Kd = Kb if Kd is None else int(Kd)
+        out = torch.empty(splits, N, M, dtype=torch.float32, device=A.device)
+        self._bind_stream()
+        st = lib().gpl1_gemm_bf16_ex(self._h, ctypes.c_void_p(A.data_ptr()), M, Ka, A.stride(0),
+                                     ctypes.c_void_p(B.data_ptr()), N, Kd, B.stride(0),
+                                     ctypes.c_void_p(out.data_ptr()), out.stride(1), float(scale),
+                                     int(config), int(splits), out.stride(0))
+        self._check(st)
+        return out
+
+    def gemm_tuned(self):
+        """The autotuner's choices: [{shape: (M, N, Kd, Ka, max_splits), config, splits, ms}]."""
+        L = lib()
+        count = L.gpl1_gemm_tuned(self._h, 0, None, None, None, None)
+        out = []
+        for i in range(max(count, 0)):
+            shp = (ctypes.c_longlong * 5)()
+            cfg, spl, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+            L.gpl1_gemm_tuned(self._h, i, shp, ctypes.byref(cfg), ctypes.byref(spl), ctypes.byref(ms))
+            out.append({"shape": tuple(shp), "config": cfg.value, "splits": spl.value, "ms": ms.value})
         return out
 
     # ------------------------------------------------ learned warm start

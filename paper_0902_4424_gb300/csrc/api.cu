@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <vector>
@@ -27,6 +28,8 @@ struct gpl1_ctx {
   std::vector<uint8_t> host_stage;  // staging of descriptors (kept alive across async copies)
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};   // around the solver launch
+  // autotuned tensor-core products: (M, N, Kd, Ka, max_splits) -> configuration and split
+  std::map<std::vector<long long>, gpl1::GemmChoice> gemm_tuned;
 };
 
 namespace {
@@ -563,9 +566,11 @@ extern "C" gpl1_status gpl1_solve_noalloc(const gpl1_problem* prob, gpl1_dtype d
 // ---------------------------------------------------------------------------
 // gpl1_gemm_bf16: the tensor-core product of the shared-K form (gemm_tc.cu).
 
-extern "C" gpl1_status gpl1_gemm_bf16(gpl1_ctx* ctx, const void* A, long long M, long long Ka, long long lda,
-                                      const void* B, long long N, long long Kd, long long ldb, float* out,
-                                      long long ldo, float scale) {
+namespace {
+
+gpl1_status gemm_impl(gpl1_ctx* ctx, const void* A, long long M, long long Ka, long long lda, const void* B,
+                      long long N, long long Kd, long long ldb, float* out, long long ldo, float scale, int cfg,
+                      int splits, long long split_stride) {
   if (!ctx) return GPL1_ERR_INVALID_ARG;
   if (!A || !B || !out) return fail(ctx, GPL1_ERR_INVALID_ARG, "NULL pointer");
   if (M < 1 || N < 1 || Ka < 64 || Kd < 64 || Ka % 64 || Kd % 64)
@@ -588,10 +593,13 @@ extern "C" gpl1_status gpl1_gemm_bf16(gpl1_ctx* ctx, const void* A, long long M,
   if (st) return st;
   int* err = static_cast<int*>(ctx->ws);
   GPL1_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream), "cudaMemsetAsync");
-  const int bn = N > 128 ? 256 : 128;
-  const int e = launch_gemm_bf16(ctx->encode, A, static_cast<int>(M), static_cast<int>(Ka), lda, B,
-                                 static_cast<int>(N), static_cast<int>(Kd), ldb, out, ldo, scale, err,
-                                 10LL * 1000 * 1000 * 1000, bn, ctx->stream);
+  if (cfg < 0 || cfg >= kGemmConfigs) return fail(ctx, GPL1_ERR_INVALID_ARG, "config must lie in [0, %d)", kGemmConfigs);
+  if (splits < 1 || splits > Kd / 64) return fail(ctx, GPL1_ERR_INVALID_ARG, "splits must lie in [1, Kd / 64]");
+  if (splits > 1 && split_stride < ldo * N)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "split_stride must hold a whole N x ldo output");
+  const int e = launch_gemm_bf16_cfg(ctx->encode, A, static_cast<int>(M), static_cast<int>(Ka), lda, B,
+                                     static_cast<int>(N), static_cast<int>(Kd), ldb, out, ldo, scale, err,
+                                     10LL * 1000 * 1000 * 1000, cfg, splits, split_stride, ctx->stream);
   if (e == -1) return fail(ctx, GPL1_ERR_CUDA, "tensor map encoding failed");
   if (e != 0) return cuda_fail(ctx, static_cast<cudaError_t>(e), "gemm launch");
   int herr = 0;
@@ -601,8 +609,67 @@ extern "C" gpl1_status gpl1_gemm_bf16(gpl1_ctx* ctx, const void* A, long long M,
   return GPL1_OK;
 }
 
+}  // namespace
+
+extern "C" gpl1_status gpl1_gemm_bf16(gpl1_ctx* ctx, const void* A, long long M, long long Ka, long long lda,
+                                      const void* B, long long N, long long Kd, long long ldb, float* out,
+                                      long long ldo, float scale) {
+  return gemm_impl(ctx, A, M, Ka, lda, B, N, Kd, ldb, out, ldo, scale, N > 128 ? 1 : 0, 1, 0);
+}
+
+extern "C" gpl1_status gpl1_gemm_bf16_ex(gpl1_ctx* ctx, const void* A, long long M, long long Ka, long long lda,
+                                         const void* B, long long N, long long Kd, long long ldb, float* out,
+                                         long long ldo, float scale, int config, int splits,
+                                         long long split_stride) {
+  return gemm_impl(ctx, A, M, Ka, lda, B, N, Kd, ldb, out, ldo, scale, config, splits, split_stride);
+}
+
+extern "C" int gpl1_gemm_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* config, int* splits,
+                               float* ms) {
+  if (!ctx) return -1;
+  const int count = static_cast<int>(ctx->gemm_tuned.size());
+  if (index < 0 || index >= count) return count;
+  auto it = ctx->gemm_tuned.begin();
+  std::advance(it, index);
+  if (shape)
+    for (int q = 0; q < 5; ++q) shape[q] = it->first[q];
+  if (config) *config = it->second.cfg;
+  if (splits) *splits = it->second.splits;
+  if (ms) *ms = it->second.ms;
+  return count;
+}
+
 // ---------------------------------------------------------------------------
 // gpl1_solve_shared_k: nrhs instances sharing one BF16 K (shared_k.cu).
+
+namespace {
+
+constexpr int kMaxSplits = 8;   // split-K partial slices of the second product
+
+// The configuration of one product of the shared-K form: from the context's
+// cache, else tuned on the given operands (autotune.cu) and cached.
+gpl1_status tuned_gemm(gpl1_ctx* ctx, const void* A, long long M, long long Ka, long long lda, const void* B,
+                       long long Nc, long long Kd, long long ldb, float* out, long long ldo, float scale, int* err,
+                       long long tmo, int max_splits, long long split_stride, GemmChoice* c) {
+  const std::vector<long long> key{M, Nc, Kd, Ka, max_splits};
+  const auto it = ctx->gemm_tuned.find(key);
+  if (it != ctx->gemm_tuned.end()) {
+    *c = it->second;
+    return GPL1_OK;
+  }
+  const int e = autotune_gemm(ctx->encode, A, static_cast<int>(M), static_cast<int>(Ka), lda, B, static_cast<int>(Nc),
+                              static_cast<int>(Kd), ldb, out, ldo, scale, err, tmo, max_splits, split_stride, 6000.0,
+                              ctx->stream, c);
+  if (e == -1) return fail(ctx, GPL1_ERR_CUDA, "tensor map");
+  if (e) return cuda_fail(ctx, static_cast<cudaError_t>(e), "autotune");
+  int ge = 0;
+  GPL1_CUDA(cudaMemcpy(&ge, err, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy");
+  if (ge) return fail(ctx, static_cast<gpl1_status>(ge), "a bounded wait in a GEMM ran out while tuning");
+  ctx->gemm_tuned[key] = *c;
+  return GPL1_OK;
+}
+
+}  // namespace
 
 extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
                                            const float* Y, long long ldy, const double* rho, const double* f_star,
@@ -615,6 +682,7 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
   if (n < 64 || p < 64 || n % 64 || p % 64)
     return fail(ctx, GPL1_ERR_UNSUPPORTED, "the shared-K form needs n and p to be multiples of 64");
   if (p > static_cast<long long>(35) * kConsumers) return fail(ctx, GPL1_ERR_UNSUPPORTED, "p exceeds %d", 35 * kConsumers);
+  if (n > static_cast<long long>(9) * kConsumers) return fail(ctx, GPL1_ERR_UNSUPPORTED, "n exceeds %d", 9 * kConsumers);
   if (ldk < p || (ldk * 2) % 16 || reinterpret_cast<uintptr_t>(K) % 16)
     return fail(ctx, GPL1_ERR_INVALID_ARG, "K rows must be 16-byte aligned, ldk >= p");
   if (ldy < n || ldx < p) return fail(ctx, GPL1_ERR_INVALID_ARG, "need ldy >= n and ldx >= p");
@@ -638,9 +706,10 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
     return o;
   };
   const size_t o_kt = take(pp * nn * 2), o_g0 = take(N * pp * 4), o_g1 = take(N * pp * 4), o_d = take(N * pp * 4);
-  const size_t o_dx = take(2 * N * 3 * pp * 2), o_kdx = take(2 * N * nn * 4), o_rs = take(N * 3 * nn * 2);
+  const size_t o_dx = take(N * 3 * pp * 2), o_kdx = take(kMaxSplits * N * nn * 4), o_rs = take(N * 3 * nn * 2);
   const size_t o_st = take(N * mr_state_bytes()), o_res = take(N * sizeof(gpl1_result));
   const size_t o_rho = take(N * 8), o_fs = take(N * 8);
+  const size_t o_xp = take(mr_exact_part_bytes(static_cast<int>(n), static_cast<int>(p), nrhs));
   st = ensure_ws(ctx, off);
   if (st) return st;
   uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
@@ -650,12 +719,13 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
   float* G[2] = {reinterpret_cast<float*>(ws + o_g0), reinterpret_cast<float*>(ws + o_g1)};
   float* D = reinterpret_cast<float*>(ws + o_d);
   uint16_t* DXs = reinterpret_cast<uint16_t*>(ws + o_dx);
-  float* KDX = reinterpret_cast<float*>(ws + o_kdx);
+  float* KD = reinterpret_cast<float*>(ws + o_kdx);   // kMaxSplits partial slices of N x n
   uint16_t* Rs = reinterpret_cast<uint16_t*>(ws + o_rs);
   void* states = ws + o_st;
   gpl1_result* rdev = reinterpret_cast<gpl1_result*>(ws + o_res);
   double* rho_d = reinterpret_cast<double*>(ws + o_rho);
   double* fs_d = reinterpret_cast<double*>(ws + o_fs);
+  void* xpart = ws + o_xp;   // column partials of the exact K x
   cudaStream_t s = ctx->stream;
   GPL1_CUDA(cudaMemsetAsync(ws, 0, 256, s), "cudaMemsetAsync");
   GPL1_CUDA(cudaMemsetAsync(G[1], 0, N * pp * 4, s), "cudaMemsetAsync");
@@ -675,29 +745,34 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
               "init");
   } else {   // x0 given: into the balls, K x0 on the tensor cores, then r0 and f0
     GPL1_CUDA(launch_mr_setup_x0(X, ldx, DXs, static_cast<int>(p), nrhs, rho_d, s), "setup x0");
-    const int e0 = launch_gemm_bf16(ctx->encode, K, static_cast<int>(n), static_cast<int>(p), ldk, DXs, 2 * nrhs,
-                                    static_cast<int>(3 * p), 3 * p, KDX, n, 1.f, gerr, tmo,
-                                    ((n + 127) / 128) * ((2LL * nrhs + 255) / 256) < ctx->num_sms ? 128 : 256, s);
+    const int e0 = launch_gemm_bf16(ctx->encode, K, static_cast<int>(n), static_cast<int>(p), ldk, DXs, nrhs,
+                                    static_cast<int>(3 * p), 3 * p, KD, n, 1.f, gerr, tmo, 128, s);
     if (e0) return e0 == -1 ? fail(ctx, GPL1_ERR_CUDA, "tensor map") : cuda_fail(ctx, static_cast<cudaError_t>(e0), "K x0");
-    GPL1_CUDA(launch_mr_setup_r(KDX, Y, ldy, Rs, static_cast<int>(n), nrhs, rho_d, f_star ? fs_d : nullptr, states,
+    GPL1_CUDA(launch_mr_setup_r(KD, Y, ldy, Rs, static_cast<int>(n), nrhs, rho_d, f_star ? fs_d : nullptr, states,
                                 sp, s),
               "setup r0");
   }
-  auto bn_for = [&](long long M, long long Nc) {
-    return ((M + 127) / 128) * ((Nc + 255) / 256) < ctx->num_sms ? 128 : 256;
-  };
+  // the two products' configurations, tuned once per shape and context on these operands
+  GemmChoice c1, c2;
+  if ((st = tuned_gemm(ctx, Kt, p, n, n, Rs, nrhs, 3 * n, 3 * n, G[0], p, 2.f, gerr, tmo, 1, 0, &c1))) return st;
+  if ((st = tuned_gemm(ctx, K, n, p, ldk, DXs, nrhs, 3 * p, 3 * p, KD, n, 1.f, gerr, tmo, kMaxSplits,
+                       static_cast<long long>(N * nn), &c2)))
+    return st;
   for (int k = 0; k < prm->max_iter; ++k) {
     float* Gc = G[k & 1];
     float* Gp = G[(k + 1) & 1];
-    int e = launch_gemm_bf16(ctx->encode, Kt, static_cast<int>(p), static_cast<int>(n), n, Rs, nrhs,
-                             static_cast<int>(3 * n), 3 * n, Gc, p, 2.f, gerr, tmo, bn_for(p, nrhs), s);
+    int e = launch_gemm_bf16_cfg(ctx->encode, Kt, static_cast<int>(p), static_cast<int>(n), n, Rs, nrhs,
+                                 static_cast<int>(3 * n), 3 * n, Gc, p, 2.f, gerr, tmo, c1.cfg, 1, 0, s);
     if (e) return e == -1 ? fail(ctx, GPL1_ERR_CUDA, "tensor map") : cuda_fail(ctx, static_cast<cudaError_t>(e), "gemm 1");
     GPL1_CUDA(launch_mr_phase_p(Gc, Gp, X, ldx, D, DXs, static_cast<int>(p), nrhs, k, states, sp, s), "phase P");
-    e = launch_gemm_bf16(ctx->encode, K, static_cast<int>(n), static_cast<int>(p), ldk, DXs, 2 * nrhs,
-                         static_cast<int>(3 * p), 3 * p, KDX, n, 1.f, gerr, tmo, bn_for(n, 2LL * nrhs), s);
+    e = launch_gemm_bf16_cfg(ctx->encode, K, static_cast<int>(n), static_cast<int>(p), ldk, DXs, nrhs,
+                             static_cast<int>(3 * p), 3 * p, KD, n, 1.f, gerr, tmo, c2.cfg, c2.splits,
+                             static_cast<long long>(N * nn), s);
     if (e) return e == -1 ? fail(ctx, GPL1_ERR_CUDA, "tensor map") : cuda_fail(ctx, static_cast<cudaError_t>(e), "gemm 2");
-    GPL1_CUDA(launch_mr_phase_l(KDX, Kt, Y, ldy, X, ldx, D, Rs, static_cast<int>(n), static_cast<int>(p), nrhs, k,
-                                states, sp, rdev, done_count, s),
+    GPL1_CUDA(launch_mr_exact_kx(Kt, X, ldx, xpart, static_cast<int>(n), static_cast<int>(p), nrhs, states, s),
+              "exact K x");
+    GPL1_CUDA(launch_mr_phase_l(KD, c2.splits, static_cast<long long>(N * nn), xpart, Y, ldy, X, ldx, D, Rs,
+                                static_cast<int>(n), static_cast<int>(p), nrhs, k, states, sp, rdev, done_count, s),
               "phase L");
     if ((k & 3) == 3 || k + 1 == prm->max_iter) {
       int hd[2] = {0, 0};

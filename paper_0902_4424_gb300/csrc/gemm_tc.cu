@@ -13,12 +13,26 @@
 // accumulation.  The transposed store makes each right-hand side's vector
 // contiguous; the row-major one keeps batch-major activations batch-major.
 //
-// One CTA per 128 x BN tile, 128 threads: thread 0 issues the TMA loads of a
-// 4-stage ring (128-byte swizzle), thread 32 issues the MMAs (128 x BN x 16
-// per instruction, FP32 accumulator in tensor memory), and all four warps
-// read the accumulator back (warp w owns tensor-memory lanes 32w .. 32w+31,
-// i.e. rows m0 + 32w ..) and store it.  Every wait is bounded; a wait that
-// runs out sets *err and the CTA still releases its tensor memory.
+// One CTA per 128 x BN tile and split of the contraction, 128 threads: thread 0
+// issues the TMA loads of an ST-stage ring (128-byte swizzle), thread 32 issues
+// the MMAs (128 x BN x 16 per instruction, FP32 accumulator in tensor memory),
+// and all four warps read the accumulator back (warp w owns tensor-memory
+// lanes 32w .. 32w+31, i.e. rows m0 + 32w ..) and store it.  Every wait is
+// bounded; a wait that runs out sets *err and the CTA still releases its
+// tensor memory.
+//
+// Split-K: with S splits, CTA (x, y, z) sums k-blocks [z KB / S, (z+1) KB / S)
+// and writes its partial product to out + z * split_stride; the S partials
+// add up to the product (the consumer sums them in a fixed order, so results
+// do not depend on scheduling).  This fills the 152 SMs when M x N has few
+// tiles and the contraction is long.
+//
+// Configurations (the autotuner of the shared-K solve picks one per shape):
+//   0: BN 128, 4 stages (132 KB shared memory, one CTA per SM)
+//   1: BN 256, 4 stages (193 KB, one CTA per SM)
+//   2: BN 128, 3 stages (97 KB, two CTAs per SM: one's epilogue overlaps the
+//      other's main loop)
+//   3: BN 128, 6 stages (193 KB, one CTA per SM: deeper load pipeline)
 #include <cudaTypedefs.h>
 
 #include "launch.h"
@@ -26,7 +40,7 @@
 
 namespace gpl1 {
 
-constexpr int kTcBM = 128, kTcBK = 64, kTcStages = 4;
+constexpr int kTcBM = 128, kTcBK = 64;
 
 struct GemmArgs {
   int M, N, Kd, Ka;
@@ -36,14 +50,16 @@ struct GemmArgs {
   int* err;
   long long timeout_ns;
   int trans_out;
+  int splits;
+  long long split_stride;
 };
 
-template <int BN>
+template <int BN, int ST>
 struct GemmLayout {
   static constexpr int kA = kTcBM * kTcBK * 2;   // 16 KB
   static constexpr int kB = BN * kTcBK * 2;      // 16 or 32 KB
   static constexpr int kStage = kA + kB;         // a multiple of 1024 (swizzle atoms)
-  static constexpr size_t kBytes = static_cast<size_t>(kTcStages) * kStage + 128 + 1024;
+  static constexpr size_t kBytes = static_cast<size_t>(ST) * kStage + 128 + 1024;
 };
 
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
@@ -54,10 +70,11 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, uin
   return true;
 }
 
-template <int BN>
+template <int BN, int ST>
 __global__ void __launch_bounds__(128, 1) gemm_bf16_tn(const __grid_constant__ CUtensorMap ta,
                                                        const __grid_constant__ CUtensorMap tb, const GemmArgs g) {
-  using L = GemmLayout<BN>;
+  constexpr int kTcStages = ST;
+  using L = GemmLayout<BN, ST>;
   extern __shared__ uint8_t gemm_raw[];
   uint8_t* const base =
       reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gemm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -68,7 +85,11 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn(const __grid_constant__ C
   int* const state = reinterpret_cast<int*>(tmem_slot + 1);   // [0] error, [1] loads issued, [2] stages consumed
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * BN;
-  const int KB = g.Kd / kTcBK;
+  // this CTA's k-blocks: [kb0, kb0 + KB) of the Kd / 64 in all
+  const int KT = g.Kd / kTcBK, z = blockIdx.z;
+  const int kb0 = static_cast<int>(static_cast<long long>(z) * KT / g.splits);
+  const int KB = static_cast<int>(static_cast<long long>(z + 1) * KT / g.splits) - kb0;
+  float* const out = g.out + static_cast<long long>(z) * g.split_stride;
   const uint64_t lim = static_cast<uint64_t>(g.timeout_ns);
 
   if (threadIdx.x == 0) {
@@ -99,8 +120,8 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn(const __grid_constant__ C
       }
       uint8_t* const sa = base + s * L::kStage;
       mbar_arrive_expect_tx(&full[s], L::kStage);
-      tma_load_2d(sa, &ta, &full[s], (kb * kTcBK) % g.Ka, m0);
-      tma_load_2d(sa + L::kA, &tb, &full[s], kb * kTcBK, n0);
+      tma_load_2d(sa, &ta, &full[s], ((kb0 + kb) * kTcBK) % g.Ka, m0);
+      tma_load_2d(sa + L::kA, &tb, &full[s], (kb0 + kb) * kTcBK, n0);
     }
     state[1] = kb;
   } else if (warp == 1 && lane == 0) {   // MMA issuer
@@ -139,10 +160,10 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn(const __grid_constant__ C
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const int n = n0 + c0 + q;
-            if (n < g.N) g.out[static_cast<long long>(n) * g.ldo + m] = g.scale * v[q];
+            if (n < g.N) out[static_cast<long long>(n) * g.ldo + m] = g.scale * v[q];
           }
         } else {
-          float* row = g.out + static_cast<long long>(m) * g.ldo + n0 + c0;
+          float* row = out + static_cast<long long>(m) * g.ldo + n0 + c0;
 #pragma unroll
           for (int q = 0; q < 16; ++q)
             if (n0 + c0 + q < g.N) row[q] = g.scale * v[q];
@@ -175,28 +196,53 @@ CUresult encode_kmajor(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, 
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-template <int BN>
-cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t stream) {
-  const size_t smem = GemmLayout<BN>::kBytes;
-  cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tn<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+template <int BN, int ST>
+cudaError_t launch_cfg(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, cudaStream_t stream) {
+  const size_t smem = GemmLayout<BN, ST>::kBytes;
+  // the attribute is set once per instantiation and device (the context is bound to one device)
+  static int set_for = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const dim3 grid((g.M + kTcBM - 1) / kTcBM, (g.N + BN - 1) / BN);
-  gemm_bf16_tn<BN><<<grid, 128, smem, stream>>>(ta, tb, g);
+  if (set_for != dev) {
+    e = cudaFuncSetAttribute(gemm_bf16_tn<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    set_for = dev;
+  }
+  const dim3 grid((g.M + kTcBM - 1) / kTcBM, (g.N + BN - 1) / BN, g.splits);
+  gemm_bf16_tn<BN, ST><<<grid, 128, smem, stream>>>(ta, tb, g);
   return cudaGetLastError();
 }
 
 }  // namespace
 
+int gemm_cfg_bn(int cfg) { return cfg == 1 ? 256 : 128; }
+
+int launch_gemm_bf16_cfg(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* A, int M, int Ka, long long lda,
+                         const void* B, int N, int Kd, long long ldb, float* out, long long ldo, float scale,
+                         int* err, long long timeout_ns, int cfg, int splits, long long split_stride,
+                         cudaStream_t stream, int trans_out) {
+  if (cfg < 0 || cfg >= kGemmConfigs || splits < 1 || splits > Kd / kTcBK) return static_cast<int>(cudaErrorInvalidValue);
+  CUtensorMap ta, tb;
+  if (encode_kmajor(enc, &ta, A, M, Ka, lda, kTcBM) != CUDA_SUCCESS) return -1;
+  if (encode_kmajor(enc, &tb, B, N, Kd, ldb, gemm_cfg_bn(cfg)) != CUDA_SUCCESS) return -1;
+  GemmArgs g{M, N, Kd, Ka, out, ldo, scale, err, timeout_ns, trans_out, splits, split_stride};
+  cudaError_t e;
+  switch (cfg) {
+    case 1: e = launch_cfg<256, 4>(ta, tb, g, stream); break;
+    case 2: e = launch_cfg<128, 3>(ta, tb, g, stream); break;
+    case 3: e = launch_cfg<128, 6>(ta, tb, g, stream); break;
+    default: e = launch_cfg<128, 4>(ta, tb, g, stream); break;
+  }
+  return static_cast<int>(e);
+}
+
 int launch_gemm_bf16(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* A, int M, int Ka, long long lda,
                      const void* B, int N, int Kd, long long ldb, float* out, long long ldo, float scale, int* err,
                      long long timeout_ns, int bn, cudaStream_t stream, int trans_out) {
-  CUtensorMap ta, tb;
-  if (encode_kmajor(enc, &ta, A, M, Ka, lda, kTcBM) != CUDA_SUCCESS) return -1;
-  if (encode_kmajor(enc, &tb, B, N, Kd, ldb, bn) != CUDA_SUCCESS) return -1;
-  GemmArgs g{M, N, Kd, Ka, out, ldo, scale, err, timeout_ns, trans_out};
-  const cudaError_t e = bn == 256 ? launch_bn<256>(ta, tb, g, stream) : launch_bn<128>(ta, tb, g, stream);
-  return static_cast<int>(e);
+  return launch_gemm_bf16_cfg(enc, A, M, Ka, lda, B, N, Kd, ldb, out, ldo, scale, err, timeout_ns, bn == 256 ? 1 : 0,
+                              1, 0, stream, trans_out);
 }
 
 }  // namespace gpl1

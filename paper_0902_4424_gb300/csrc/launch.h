@@ -31,6 +31,26 @@ long long project_max_p(int dtype);
 int launch_gemm_bf16(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* A, int M, int Ka, long long lda,
                      const void* B, int N, int Kd, long long ldb, float* out, long long ldo, float scale, int* err,
                      long long timeout_ns, int bn, cudaStream_t stream, int trans_out = 1);
+// The same with a kernel configuration (0..kGemmConfigs-1, see gemm_tc.cu) and a
+// split of the contraction into `splits` parts: part z goes to out + z * split_stride.
+constexpr int kGemmConfigs = 4;
+int gemm_cfg_bn(int cfg);
+int launch_gemm_bf16_cfg(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* A, int M, int Ka, long long lda,
+                         const void* B, int N, int Kd, long long ldb, float* out, long long ldo, float scale,
+                         int* err, long long timeout_ns, int cfg, int splits, long long split_stride,
+                         cudaStream_t stream, int trans_out = 1);
+
+// Autotuner (autotune.cu): the fastest configuration and split (<= max_splits,
+// partial z at out + z * split_stride) of one product, timed on its operands;
+// sum_gbs is the bandwidth at which the consumer sums the partials (its cost is
+// added).  Returns a cudaError_t or -1 (tensor map).
+struct GemmChoice {
+  int cfg, splits;
+  float ms;
+};
+int autotune_gemm(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* A, int M, int Ka, long long lda, const void* B,
+                  int N, int Kd, long long ldb, float* out, long long ldo, float scale, int* err, long long timeout_ns,
+                  int max_splits, long long split_stride, double sum_gbs, cudaStream_t stream, GemmChoice* best);
 
 }  // namespace gpl1
 
@@ -43,10 +63,13 @@ cudaError_t launch_mr_init(const float* Y, long long ldy, float* X, long long ld
 cudaError_t launch_mr_phase_p(const float* G, const float* Gprev, const float* X, long long ldx, float* D,
                               uint16_t* DXs, int p, int nrhs, int k, void* states, const SolveParams& prm,
                               cudaStream_t s);
-cudaError_t launch_mr_phase_l(const float* KDX, const void* Kt, const float* Y, long long ldy, float* X,
-                              long long ldx, const float* D, uint16_t* Rs, int n, int p, int nrhs, int k,
-                              void* states, const SolveParams& prm, gpl1_result* res, int* done_count,
-                              cudaStream_t s);
+cudaError_t launch_mr_phase_l(float* KD, int splits, long long split_stride, const void* xpart, const float* Y,
+                              long long ldy, float* X, long long ldx, const float* D, uint16_t* Rs, int n, int p,
+                              int nrhs, int k, void* states, const SolveParams& prm, gpl1_result* res,
+                              int* done_count, cudaStream_t s);
+size_t mr_exact_part_bytes(int n, int p, int nrhs);
+cudaError_t launch_mr_exact_kx(const void* Kt, const float* X, long long ldx, void* xpart, int n, int p, int nrhs,
+                               const void* states, cudaStream_t s);
 cudaError_t launch_transpose_bf16(const void* K, long long ldk, void* Kt, int n, int p, cudaStream_t s);
 cudaError_t launch_mr_setup_x0(float* X, long long ldx, uint16_t* DXs, int p, int nrhs, const double* rho,
                                cudaStream_t s);

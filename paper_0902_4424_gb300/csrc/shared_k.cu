@@ -2,8 +2,8 @@
 // (BF16) and differ in y and rho, solved together.  Their gradients
 // g_b = 2 K^T r_b and their products K d_b, K x_b are then the matrix products
 //
-//   G   = 2 R K        (nrhs x p)   on the tensor cores as  K^T [R]^T
-//   KDX = [D; X] K^T   (2 nrhs x n) on the tensor cores as  K [D; X]^T
+//   G  = 2 R K      (nrhs x p)   on the tensor cores as  K^T R^T
+//   KD = D K^T      (nrhs x n)   on the tensor cores as  K D^T
 //
 // (gemm_tc.cu), with the FP32 vectors carried as three BF16 terms
 // (hi + mid + lo = the FP32 value to 2^-24), so a BF16 K gives FP32-accurate
@@ -12,20 +12,29 @@
 //
 //   mr_phase_p: z^T z, g^T x, ||g||_inf; Alg. SS; v = x - alpha g; the
 //     projection threshold (block_l1_tau_fixed_point, as in the single solve);
-//     d = P(v) - x; g^T d, ||d||^2; the BF16 terms of d and x for the second
+//     d = P(v) - x; g^T d, ||d||^2; the BF16 terms of d for the second
 //     product.
-//   mr_phase_l: f, r^T K d, ||K d||^2 from K x and K d; the Armijo test of
-//     Alg. GP on the exact expansion (FP64, lead thread); x += lam d,
-//     r += lam K d and its BF16 terms for the next gradient; Alg. SS state;
-//     the stop rules.
+//   mr_phase_l: the sum of the second product's split-K partials; f,
+//     r^T K d, ||K d||^2; the Armijo test of Alg. GP on the exact expansion
+//     (FP64, lead thread); x += lam d, r += lam K d (the update of Alg. GP,
+//     Step 6) and its BF16 terms for the next gradient; Alg. SS state; the
+//     stop rules.
 //
-// Near the stop (estimated gap below 1000 tol, or progress below 1e-4 f),
-// mr_phase_l forms K x itself instead of taking it from the tensor-core
-// product: the FP32 accumulation over 3p terms there leaves about 1e-6 of
-// |K x| in each entry, which r^T dKx turns into an error of f far above
-// tol f* when f* << ||y||^2.  The iterate is sparse by then (the l1 ball), so
-// K x = sum over the support of x_j (column j of K = row j of the stored K^T),
-// with exact products and two-sums: the same compensated sum as the single
+// r is carried from iteration to iteration (its BF16 terms hold the FP32
+// value exactly), so the second product needs K d only: half the tensor work
+// of forming K x again.  The carried r drifts from K x - y by the rounding of
+// the updates and the FP32 accumulation error of each K d (about 1e-6 of
+// lam |K d|); summed over the path from x0 that is about 1e-6 |K x|, and
+// r^T dKx turns it into an error of f far above tol f* when f* << ||y||^2.
+// So near the stop (estimated gap below 1000 tol, or progress below 1e-4 f)
+// r restarts from an exact K x (mr_exact_kx, between the second product and
+// mr_phase_l), on the first iteration there and every 8th after: the drift
+// since a restart is 1e-6 of the few small steps near the optimum.  The
+// relative-gap stop is only taken on an iteration whose r was restarted: met
+// on a carried r, it schedules a restart for the next iteration and is
+// decided there.  The iterate is sparse by then (the l1 ball), so K x = sum
+// over the support of x_j (column j of K = row j of the stored K^T), with
+// exact products and two-sums: the same compensated sum as the single
 // solve's pass B near its stop.
 //
 // As in the single solve, x is kept inside the ball (an exact ||x||_1 check
@@ -43,17 +52,26 @@ struct MrState {
   SSState<float> ss;
   float ah, th, tl, vbound, gmaxf, xscale;
   float rho_hi, rho_lo;
-  int inside, nz, iters, backtracks, stop, status, done, acc;
+  int inside, nz, iters, backtracks, stop, status, done, acc, acc_age;
   double f_cur, gap_den, f_star, rho, lam, gd, dd, gx;
   double fhist[kMaxM];
 };
 
+// The staged vector comes last: a launch allocates only its first
+// ceil(p / 480) * 480 entries, so that for p = 8192 four CTAs share an SM.
 struct MrSmem {
-  float xs[kMrVmax * kConsumers];
   ProjSmem ps;
   Scratch sc;
   int flag[4];
+  float xs[2 * kMrVmax * kConsumers];
 };
+
+// Phase P stages two vectors there (x, later v, and g; each neu * 480
+// floats); the other kernels use the first.
+size_t mr_smem_bytes(int p, int vectors) {
+  const size_t neu = (static_cast<size_t>(p) + kConsumers - 1) / kConsumers;
+  return offsetof(MrSmem, xs) + static_cast<size_t>(vectors) * neu * kConsumers * sizeof(float);
+}
 
 size_t mr_state_bytes() { return sizeof(MrState); }
 
@@ -139,7 +157,8 @@ __global__ void __launch_bounds__(kConsumers) mr_init(const float* Y, long long 
 }
 
 // Given x0 (rows of X): project it onto its ball where it lies outside (Alg.
-// GP starts in Omega), then lay out its BF16 terms (and d = 0) for K [D; X]^T.
+// GP starts in Omega), then lay out its BF16 terms (in the rows of the d
+// terms) for the product K x0.
 __global__ void __launch_bounds__(kConsumers) mr_setup_x0(float* X, long long ldx, uint16_t* DXs, int p, int nrhs,
                                                           const double* rho) {
   const int b = blockIdx.x, tid = threadIdx.x;
@@ -163,8 +182,7 @@ __global__ void __launch_bounds__(kConsumers) mr_setup_x0(float* X, long long ld
   const SmemAcc<float, kMrVmax> acc{xs, neu};
   const TauResult t = block_l1_tau_fixed_point<float>(acc, rho[b], rho_p, 0.f, sm.ps, sm.sc);
   const TauPair tp{t.th, t.tl};
-  uint16_t* dd_s = DXs + static_cast<long long>(b) * 3 * p;
-  uint16_t* xx_s = DXs + static_cast<long long>(nrhs + b) * 3 * p;
+  uint16_t* xx_s = DXs + static_cast<long long>(b) * 3 * p;
   for (int e = 0; e < neu; ++e) {
     const int j = tid + e * kConsumers;
     if (j >= p) break;
@@ -177,7 +195,6 @@ __global__ void __launch_bounds__(kConsumers) mr_setup_x0(float* X, long long ld
     xx_s[j] = h;
     xx_s[p + j] = m;
     xx_s[2 * p + j] = l;
-    dd_s[j] = dd_s[p + j] = dd_s[2 * p + j] = 0;
   }
 }
 
@@ -187,7 +204,7 @@ __global__ void __launch_bounds__(kConsumers) mr_setup_r(const float* KDX, const
                                                          const double* fstar, MrState* st, SolveParams prm) {
   const int b = blockIdx.x, tid = threadIdx.x;
   __shared__ Scratch sc;
-  const float* kx = KDX + static_cast<long long>(nrhs + b) * n;
+  const float* kx = KDX + static_cast<long long>(b) * n;
   const float* y = Y + b * ldy;
   uint16_t* rs = Rs + static_cast<long long>(b) * 3 * n;
   F2 ff{0.f, 0.f}, yy{0.f, 0.f};
@@ -244,29 +261,42 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
   if (S.done) return;   // the same value in every thread of the CTA
   extern __shared__ uint8_t mr_raw[];
   MrSmem& sm = *reinterpret_cast<MrSmem*>(mr_raw);
-  float* const xs = sm.xs;
   const int neu = (p + kConsumers - 1) / kConsumers;
+  // staged in shared memory, element e of this thread = column tid + e * 480:
+  // xs (x, later v = x - alpha g) and gs (g)
+  float* const xs = sm.xs;
+  float* const gs = xs + neu * kConsumers;
   const float* g = G + static_cast<long long>(b) * p;
   const float* gp = Gprev + static_cast<long long>(b) * p;
   const float* x = X + b * ldx;
   // z^T z, g^T x, max |g|, ||x||_1
   F2 zz{0.f, 0.f}, gx{0.f, 0.f}, l1{0.f, 0.f};
   float pm = 0.f;
-  for (int e = 0; e < neu; ++e) {
-    const int j = tid + e * kConsumers;
-    float xv = 0.f;
-    if (j < p) {
-      const float gv = g[j];
-      xv = x[j];
+  constexpr int CH = 6;   // the loads of a chunk are issued together
+  for (int e0 = 0; e0 < neu; e0 += CH) {
+    float gv[CH], gq[CH], xv[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int j = tid + (e0 + c) * kConsumers;
+      const bool in = e0 + c < neu && j < p;
+      gv[c] = in ? g[j] : 0.f;
+      xv[c] = in ? x[j] : 0.f;
+      gq[c] = in && k > 0 ? gp[j] : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      if (e0 + c >= neu) break;
       if (k > 0) {
-        const float z = gv - gp[j];
+        const float z = gv[c] - gq[c];
         zz = f2_fma(zz, z, z);
       }
-      gx = f2_fma(gx, gv, xv);
-      l1 = f2_add(l1, fabsf(xv));
-      pm = fmaxf(pm, fabsf(gv));
+      gx = f2_fma(gx, gv[c], xv[c]);
+      l1 = f2_add(l1, fabsf(xv[c]));
+      pm = fmaxf(pm, fabsf(gv[c]));
+      const int o = (e0 + c) * kConsumers + tid;
+      xs[o] = xv[c];
+      gs[o] = gv[c];
     }
-    xs[e * kConsumers + tid] = xv;
   }
   F2 red[3] = {zz, gx, l1};
   unsigned mx = __float_as_uint(pm);
@@ -299,8 +329,8 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
   const F2 rho_p{S.rho_hi, S.rho_lo};
   if (k == 0) {   // alpha_0 = clamp(1 / ||P(x0 - g0)||_inf)  (rule 1: of P(.) - x0)
     for (int e = 0; e < neu; ++e) {
-      const int j = tid + e * kConsumers;
-      xs[e * kConsumers + tid] = j < p ? fmaf(-1.f, g[j], xs[e * kConsumers + tid] * xsc) : 0.f;
+      const int o = e * kConsumers + tid;
+      xs[o] = fmaf(-1.f, gs[o], xs[o] * xsc);   // 0 past p (g and x staged as 0 there)
     }
     consumer_sync();
     const SmemAcc<float, kMrVmax> acc{xs, neu};
@@ -326,9 +356,26 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
     consumer_sync();
   }
   const float ah = S.ah;
-  for (int e = 0; e < neu; ++e) {
-    const int j = tid + e * kConsumers;
-    xs[e * kConsumers + tid] = j < p ? fmaf(-ah, g[j], x[j] * xsc) : 0.f;
+  if (k == 0) {   // xs holds x0 - g0 here: x from memory
+    for (int e0 = 0; e0 < neu; e0 += CH) {
+      float xv[CH];
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int j = tid + (e0 + c) * kConsumers;
+        xv[c] = e0 + c < neu && j < p ? x[j] : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        if (e0 + c >= neu) break;
+        const int o = (e0 + c) * kConsumers + tid;
+        xs[o] = fmaf(-ah, gs[o], xv[c] * xsc);
+      }
+    }
+  } else {
+    for (int e = 0; e < neu; ++e) {
+      const int o = e * kConsumers + tid;
+      xs[o] = fmaf(-ah, gs[o], xs[o] * xsc);
+    }
   }
   consumer_sync();
   const SmemAcc<float, kMrVmax> vacc{xs, neu};
@@ -339,12 +386,12 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
     const TauPair tp{th, tl};
     F2 v3[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     for (int e = 0; e < neu; ++e) {
-      const int j = tid + e * kConsumers;
-      const float vv = xs[e * kConsumers + tid];
+      const int j = tid + e * kConsumers, o = e * kConsumers + tid;
+      const float vv = xs[o];
       if (j < p && !tp.below(fabsf(vv))) {
         const float s = vv > 0.f ? 1.f : -1.f;
         v3[0] = f2_add(v3[0], s * (x[j] * xsc));
-        v3[1] = f2_add(v3[1], s * g[j]);
+        v3[1] = f2_add(v3[1], s * gs[o]);
         v3[2] = f2_add(v3[2], 1.f);
       }
     }
@@ -366,28 +413,34 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
     th = sm.sc.tp[2];
     tl = sm.sc.tp[3];
   }
-  // direction, its sums, and the BF16 terms of d and x for K [D; X]^T
+  // direction, its sums, and the BF16 terms of d for K D^T
   float* d = D + static_cast<long long>(b) * p;
   uint16_t* dd_s = DXs + static_cast<long long>(b) * 3 * p;
-  uint16_t* xx_s = DXs + static_cast<long long>(nrhs + b) * 3 * p;
   F2 sgd{0.f, 0.f}, sdd{0.f, 0.f};
   unsigned nz = 0;
-  for (int j = tid; j < p; j += kConsumers) {
-    const float xj = x[j] * xsc, gj = g[j];
-    const float dj = mr_dir(xj, gj, ah, th, tl, tv.inside);
-    d[j] = dj;
-    sgd = f2_fma(sgd, gj, dj);
-    sdd = f2_fma(sdd, dj, dj);
-    nz |= dj != 0.f ? 1u : 0u;
-    uint16_t h, m, l;
-    split3(dj, h, m, l);
-    dd_s[j] = h;
-    dd_s[p + j] = m;
-    dd_s[2 * p + j] = l;
-    split3(xj, h, m, l);
-    xx_s[j] = h;
-    xx_s[p + j] = m;
-    xx_s[2 * p + j] = l;
+  for (int e0 = 0; e0 < neu; e0 += CH) {
+    float xr[CH];   // x from memory: a chunk's loads are issued before its stores
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int j = tid + (e0 + c) * kConsumers;
+      xr[c] = e0 + c < neu && j < p ? x[j] : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int e = e0 + c, j = tid + e * kConsumers, o = e * kConsumers + tid;
+      if (e >= neu || j >= p) break;
+      const float xj = xr[c] * xsc, gj = gs[o];
+      const float dj = mr_dir(xj, gj, ah, th, tl, tv.inside);
+      d[j] = dj;
+      sgd = f2_fma(sgd, gj, dj);
+      sdd = f2_fma(sdd, dj, dj);
+      nz |= dj != 0.f ? 1u : 0u;
+      uint16_t h, m, l;
+      split3(dj, h, m, l);
+      dd_s[j] = h;
+      dd_s[p + j] = m;
+      dd_s[2 * p + j] = l;
+    }
   }
   F2 v2[2] = {sgd, sdd};
   unsigned nzm = nz;
@@ -402,21 +455,115 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
   }
 }
 
-constexpr int kMrSupport = 2048;   // support entries kept for the accurate K x
+constexpr int kMrExactEvery = 8;   // near the stop, r restarts from the exact K x every 8 iterations
 constexpr int kMrRowsPerThread = 9; // n <= 9 * 480 rows for the accurate K x
 
-__global__ void __launch_bounds__(kConsumers) mr_phase_l(const float* KDX, const uint16_t* Kt, const float* Y,
-                                                         long long ldy, float* X, long long ldx, const float* D,
-                                                         uint16_t* Rs, int n, int p, int nrhs, int k, MrState* st,
-                                                         SolveParams prm, gpl1_result* res, int* done_count) {
+// Exact K x for the instances that restart r this iteration, split over
+// S = ceil(p / 1024) CTAs per instance by columns: CTA (b, s) takes the nonzero
+// x_j (x scaled into the ball, as phase P used it) of columns
+// [s p / S, (s+1) p / S) in increasing j, and sums x_j K_:j (row j of the
+// stored K^T) into float pairs, exactly up to the pair's 2^-48: each product
+// K_ij x_j is exact as (p, e) (FMA) and the running sum takes p by an
+// error-free two-sum, its error and e accumulating in the low word.  A thread
+// owns 8 consecutive rows (one 16-byte load of K^T per column).  Phase L sums
+// the S partials of a row in order of s.
+constexpr int kMrExactCols = 1024;   // columns per CTA of mr_exact_kx
+constexpr int kMrExactThreads = 256;
+constexpr int kMrExactGroups = 3;    // 8-row groups per thread: n <= 3 * 256 * 8 = 6144
+
+int mr_exact_splits(int p) { return (p + kMrExactCols - 1) / kMrExactCols; }
+
+__device__ __forceinline__ bool mr_restarts(const MrState& S) {
+  return !S.done && S.acc && S.acc_age % kMrExactEvery == 0;
+}
+
+__global__ void __launch_bounds__(kMrExactThreads) mr_exact_kx(const uint16_t* __restrict__ Kt,
+                                                              const float* __restrict__ X, long long ldx,
+                                                              F2* __restrict__ part, int n, int p,
+                                                              const MrState* __restrict__ st) {
+  const int b = blockIdx.x, s = blockIdx.y, S = gridDim.y, tid = threadIdx.x;
+  const MrState& M = st[b];
+  if (!mr_restarts(M)) return;   // the same value in every thread
+  __shared__ int sup_j[kMrExactCols];
+  __shared__ float sup_x[kMrExactCols];
+  __shared__ int sup_n;
+  const int j0 = static_cast<int>(static_cast<long long>(s) * p / S);
+  const int j1 = static_cast<int>(static_cast<long long>(s + 1) * p / S);
+  const float xsc = M.xscale;
+  const float* x = X + b * ldx;
+  if (tid < 32) {   // warp 0 lists the nonzeros in increasing j (ballot order)
+    int cnt = 0;
+    for (int c0 = j0; c0 < j1; c0 += 32) {
+      const int j = c0 + tid;
+      const float xv = j < j1 ? x[j] * xsc : 0.f;
+      const unsigned nzm = __ballot_sync(0xffffffffu, xv != 0.f);
+      if (xv != 0.f) {
+        const int q = cnt + __popc(nzm & ((1u << tid) - 1u));
+        sup_j[q] = j;
+        sup_x[q] = xv;
+      }
+      cnt += __popc(nzm);
+    }
+    if (tid == 0) sup_n = cnt;
+  }
+  __syncthreads();
+  const int ns = sup_n;
+  F2 acc[kMrExactGroups][8];
+#pragma unroll
+  for (int m = 0; m < kMrExactGroups; ++m)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[m][r] = F2{0.f, 0.f};
+  for (int q = 0; q < ns; ++q) {
+    const float xv = sup_x[q];
+    const uint16_t* col = Kt + static_cast<long long>(sup_j[q]) * n;   // column j of K
+#pragma unroll
+    for (int m = 0; m < kMrExactGroups; ++m) {
+      const int i0 = 8 * (tid + m * kMrExactThreads);
+      if (i0 >= n) break;
+      const uint4 w = *reinterpret_cast<const uint4*>(col + i0);
+      const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float kv = __uint_as_float(r & 1 ? (u[r >> 1] & 0xffff0000u) : (u[r >> 1] << 16));
+        const float pr = __fmul_rn(kv, xv);
+        const float pe = fmaf(kv, xv, -pr);
+        const F2 t = two_sum(acc[m][r].hi, pr);
+        acc[m][r].hi = t.hi;
+        acc[m][r].lo += t.lo + pe;
+      }
+    }
+  }
+  F2* out = part + (static_cast<long long>(b) * S + s) * n;
+#pragma unroll
+  for (int m = 0; m < kMrExactGroups; ++m) {
+    const int i0 = 8 * (tid + m * kMrExactThreads);
+    if (i0 >= n) break;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) out[i0 + r] = two_sum(acc[m][r].hi, acc[m][r].lo);
+  }
+}
+
+// The carried r_i = K x - y: its three BF16 terms add up to the FP32 value
+// exactly; on an iterate that phase P scaled back onto the ball (x -> c x),
+// K (c x) - y = c r + (c - 1) y.
+__device__ __forceinline__ F2 mr_carried_r(const uint16_t* rs, int n, int i, float xsc, float yi) {
+  const float r = (__uint_as_float(static_cast<unsigned>(rs[i]) << 16) +
+                   __uint_as_float(static_cast<unsigned>(rs[n + i]) << 16)) +
+                  __uint_as_float(static_cast<unsigned>(rs[2 * n + i]) << 16);
+  if (xsc == 1.f) return F2{r, 0.f};
+  return two_sum(__fmul_rn(xsc, r), (xsc - 1.f) * yi);
+}
+
+__global__ void __launch_bounds__(kConsumers) mr_phase_l(float* KD, int splits, long long split_stride,
+                                                         const F2* part, int xsplits, const float* Y, long long ldy,
+                                                         float* X, long long ldx, const float* D, uint16_t* Rs, int n,
+                                                         int p, int k, MrState* st, SolveParams prm,
+                                                         gpl1_result* res, int* done_count) {
   const int b = blockIdx.x, tid = threadIdx.x;
   MrState& S = st[b];
   __shared__ Scratch sc;
   __shared__ int flag[2];
   __shared__ float lamf;
-  __shared__ int sup_j[kMrSupport];
-  __shared__ float sup_x[kMrSupport];
-  __shared__ int sup_n;
   if (S.done) {   // stopped in phase P of this iteration (FW) or earlier
     if (tid == 0 && S.done == 1) {
       S.done = 2;   // record once
@@ -437,58 +584,57 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_l(const float* KDX, const
     }
     return;
   }
-  const float* kd = KDX + static_cast<long long>(b) * n;
-  const float* kx = KDX + static_cast<long long>(nrhs + b) * n;
+  float* kd = KD + static_cast<long long>(b) * n;
   const float* y = Y + b * ldy;
-  // r = K x - y: from the tensor-core product, or near the stop summed exactly
-  // over the support of x (the iterate scaled into the ball, as phase P used it)
-  bool exact = S.acc && n <= kMrRowsPerThread * kConsumers;
-  if (exact) {
-    if (tid == 0) sup_n = 0;
-    __syncthreads();
-    const float* x = X + b * ldx;
-    const float xsc = S.xscale;
-    for (int j = tid; j < p; j += kConsumers) {
-      const float xv = x[j] * xsc;
-      if (xv != 0.f) {
-        const int q = atomicAdd(&sup_n, 1);
-        if (q < kMrSupport) {
-          sup_j[q] = j;
-          sup_x[q] = xv;
-        }
-      }
-    }
-    __syncthreads();
-    exact = sup_n <= kMrSupport;   // the same decision in every thread
-  }
+  const uint16_t* rsc = Rs + static_cast<long long>(b) * 3 * n;
+  const float xsc0 = S.xscale;
+  // r = K x - y: carried, or on a restart the exact K x of mr_exact_kx (its
+  // column partials summed in order)
+  const bool exact = mr_restarts(S);
   F2 racc[kMrRowsPerThread];
-  if (exact) {
 #pragma unroll
-    for (int m = 0; m < kMrRowsPerThread; ++m) racc[m] = F2{0.f, 0.f};
-    const int ns = sup_n;
-    for (int q = 0; q < ns; ++q) {
-      const float xv = sup_x[q];
-      const uint16_t* col = Kt + static_cast<long long>(sup_j[q]) * n;   // column j of K
+  for (int m = 0; m < kMrRowsPerThread; ++m) racc[m] = F2{0.f, 0.f};
+  if (exact) {
+    const F2* pb = part + static_cast<long long>(b) * xsplits * n;
+    for (int z = 0; z < xsplits; ++z) {
 #pragma unroll
       for (int m = 0; m < kMrRowsPerThread; ++m) {
         const int i = tid + m * kConsumers;
-        if (i < n) racc[m] = f2_fma(racc[m], __uint_as_float(static_cast<unsigned>(col[i]) << 16), xv);
+        if (i < n) racc[m] = f2_add(racc[m], pb[static_cast<long long>(z) * n + i]);
       }
     }
   }
-  F2 v[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  for (int i = tid, m = 0; i < n; i += kConsumers, ++m) {
-    const float kdi = kd[i];
-    F2 r;
-    if (exact) {
-      const F2 t = two_sum(racc[m].hi, -y[i]);
-      r = two_sum(t.hi, t.lo + racc[m].lo);
-    } else {
-      r = two_sum(kx[i], -y[i]);
+  // K d (the split-K partials summed in order, the sum kept in partial 0), y and r
+  float kdv[kMrRowsPerThread], yv[kMrRowsPerThread];
+  F2 rv[kMrRowsPerThread];
+#pragma unroll
+  for (int m = 0; m < kMrRowsPerThread; ++m) {
+    const int i = tid + m * kConsumers;
+    kdv[m] = i < n ? kd[i] : 0.f;
+    yv[m] = i < n ? y[i] : 0.f;
+  }
+  for (int z = 1; z < splits; ++z) {
+#pragma unroll
+    for (int m = 0; m < kMrRowsPerThread; ++m) {
+      const int i = tid + m * kConsumers;
+      if (i < n) kdv[m] += kd[z * split_stride + i];
     }
-    v[0] = f2_fma(v[0], r.hi, r.hi + 2.f * r.lo);
-    v[1] = f2_fma(v[1], r.hi + r.lo, kdi);
-    v[2] = f2_fma(v[2], kdi, kdi);
+  }
+  F2 v[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+  for (int m = 0; m < kMrRowsPerThread; ++m) {
+    const int i = tid + m * kConsumers;
+    if (i >= n) continue;
+    if (splits > 1) kd[i] = kdv[m];
+    if (exact) {
+      const F2 t = two_sum(racc[m].hi, -yv[m]);
+      rv[m] = two_sum(t.hi, t.lo + racc[m].lo);
+    } else {
+      rv[m] = mr_carried_r(rsc, n, i, xsc0, yv[m]);
+    }
+    v[0] = f2_fma(v[0], rv[m].hi, rv[m].hi + 2.f * rv[m].lo);
+    v[1] = f2_fma(v[1], rv[m].hi + rv[m].lo, kdv[m]);
+    v[2] = f2_fma(v[2], kdv[m], kdv[m]);
   }
   unsigned dummy = 0;
   lead_reduce<3>(v, dummy, sc);
@@ -535,10 +681,17 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_l(const float* KDX, const
         S.ss.sz_prev = 2.f * lf * lf * static_cast<float>(kb2);
         S.f_cur = fnext;
         S.iters = k + 1;
+        if (S.acc) ++S.acc_age;
         if ((S.f_star >= 0.0 && fnext - S.f_star <= 1e3 * prm.tol * S.gap_den) || fk - fnext <= 1e-4 * fk) S.acc = 1;
-        if ((prm.stop_rule & GPL1_STOP_ON_REL_GAP) && S.f_star >= 0.0 && fnext - S.f_star <= prm.tol * S.gap_den) {
+        const bool gap_met =
+            (prm.stop_rule & GPL1_STOP_ON_REL_GAP) && S.f_star >= 0.0 && fnext - S.f_star <= prm.tol * S.gap_den;
+        // f from the exact K x of this iterate
+        if (gap_met && exact) {
           S.stop = GPL1_STOP_REL_GAP;
           S.done = 1;
+        } else if (gap_met) {   // f from the carried r: confirm on an exact K x next iteration
+          S.acc = 1;
+          S.acc_age = 0;
         } else if (S.iters >= prm.max_iter) {
           S.stop = GPL1_STOP_MAX_ITER;
           S.status = GPL1_ERR_NOT_CONVERGED;
@@ -556,17 +709,27 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_l(const float* KDX, const
     const float la = lamf, xsc = S.xscale;
     float* x = X + b * ldx;
     const float* d = D + static_cast<long long>(b) * p;
-    for (int j = tid; j < p; j += kConsumers) x[j] = fmaf(la, d[j], x[j] * xsc);
-    uint16_t* rs = Rs + static_cast<long long>(b) * 3 * n;
-    for (int i = tid, m = 0; i < n; i += kConsumers, ++m) {
-      F2 r;
-      if (exact) {
-        const F2 t = two_sum(racc[m].hi, -y[i]);
-        r = two_sum(t.hi, t.lo + racc[m].lo);
-      } else {
-        r = two_sum(kx[i], -y[i]);
+    constexpr int CH = 8;   // loads of a chunk are issued together, then the stores
+    for (int j0 = tid; j0 < p; j0 += CH * kConsumers) {
+      float dv[CH], xv[CH];
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int j = j0 + c * kConsumers;
+        dv[c] = j < p ? d[j] : 0.f;
+        xv[c] = j < p ? x[j] : 0.f;
       }
-      const float rn = r.hi + fmaf(la, kd[i], r.lo);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int j = j0 + c * kConsumers;
+        if (j < p) x[j] = fmaf(la, dv[c], xv[c] * xsc);
+      }
+    }
+    uint16_t* rs = Rs + static_cast<long long>(b) * 3 * n;
+#pragma unroll
+    for (int m = 0; m < kMrRowsPerThread; ++m) {
+      const int i = tid + m * kConsumers;
+      if (i >= n) continue;
+      const float rn = rv[m].hi + fmaf(la, kdv[m], rv[m].lo);
       uint16_t th3, tm3, tl3;
       split3(rn, th3, tm3, tl3);
       rs[i] = th3;
@@ -608,14 +771,12 @@ __global__ void transpose_bf16(const uint16_t* K, long long ldk, uint16_t* Kt, i
   }
 }
 
-size_t mr_phase_p_smem() { return sizeof(MrSmem); }
-
 cudaError_t launch_mr_setup_x0(float* X, long long ldx, uint16_t* DXs, int p, int nrhs, const double* rho,
                                cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(mr_setup_x0, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sizeof(MrSmem)));
   if (e != cudaSuccess) return e;
-  mr_setup_x0<<<nrhs, kConsumers, sizeof(MrSmem), s>>>(X, ldx, DXs, p, nrhs, rho);
+  mr_setup_x0<<<nrhs, kConsumers, mr_smem_bytes(p, 1), s>>>(X, ldx, DXs, p, nrhs, rho);
   return cudaGetLastError();
 }
 cudaError_t launch_mr_setup_r(const float* KDX, const float* Y, long long ldy, uint16_t* Rs, int n, int nrhs,
@@ -641,16 +802,27 @@ cudaError_t launch_mr_phase_p(const float* G, const float* Gprev, const float* X
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  mr_phase_p<<<nrhs, kConsumers, sizeof(MrSmem), s>>>(G, Gprev, X, ldx, D, DXs, p, nrhs, k,
+  mr_phase_p<<<nrhs, kConsumers, mr_smem_bytes(p, 2), s>>>(G, Gprev, X, ldx, D, DXs, p, nrhs, k,
                                                       static_cast<MrState*>(states), prm);
   return cudaGetLastError();
 }
-cudaError_t launch_mr_phase_l(const float* KDX, const void* Kt, const float* Y, long long ldy, float* X,
-                              long long ldx, const float* D, uint16_t* Rs, int n, int p, int nrhs, int k,
-                              void* states, const SolveParams& prm, gpl1_result* res, int* done_count,
-                              cudaStream_t s) {
-  mr_phase_l<<<nrhs, kConsumers, 0, s>>>(KDX, static_cast<const uint16_t*>(Kt), Y, ldy, X, ldx, D, Rs, n, p, nrhs,
-                                         k, static_cast<MrState*>(states), prm, res, done_count);
+cudaError_t launch_mr_phase_l(float* KD, int splits, long long split_stride, const void* xpart, const float* Y,
+                              long long ldy, float* X, long long ldx, const float* D, uint16_t* Rs, int n, int p,
+                              int nrhs, int k, void* states, const SolveParams& prm, gpl1_result* res,
+                              int* done_count, cudaStream_t s) {
+  mr_phase_l<<<nrhs, kConsumers, 0, s>>>(KD, splits, split_stride, static_cast<const F2*>(xpart), mr_exact_splits(p),
+                                         Y, ldy, X, ldx, D, Rs, n, p, k, static_cast<MrState*>(states), prm, res,
+                                         done_count);
+  return cudaGetLastError();
+}
+size_t mr_exact_part_bytes(int n, int p, int nrhs) {
+  return static_cast<size_t>(nrhs) * mr_exact_splits(p) * n * sizeof(F2);
+}
+cudaError_t launch_mr_exact_kx(const void* Kt, const float* X, long long ldx, void* xpart, int n, int p, int nrhs,
+                               const void* states, cudaStream_t s) {
+  const dim3 grid(nrhs, mr_exact_splits(p));
+  mr_exact_kx<<<grid, kMrExactThreads, 0, s>>>(static_cast<const uint16_t*>(Kt), X, ldx, static_cast<F2*>(xpart), n,
+                                               p, static_cast<const MrState*>(states));
   return cudaGetLastError();
 }
 cudaError_t launch_transpose_bf16(const void* K, long long ldk, void* Kt, int n, int p, cudaStream_t s) {

@@ -43,3 +43,41 @@ def test_gemm_rejects_bad_shapes(gpu_ctx):
     with pytest.raises(pkg.Gpl1Error) as e:
         gpu_ctx.gemm_bf16(A, B)                  # K not a multiple of 64
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("config", [0, 1, 2, 3])
+@pytest.mark.parametrize("splits", [1, 3, 7])
+def test_gemm_configs_and_splits_add_up(gpu_ctx, config, splits):
+    """Every kernel configuration, with the contraction split into parts whose
+    sum (taken in order, as the shared-K solve does) is the product: each part
+    within the FP32 bound of its own k-range, the sum within the bound of the whole."""
+    M, Ka, N, Kd = 300, 512, 200, 1536          # ragged M and N tiles; A wraps three times
+    rng = np.random.default_rng(1000 * config + splits)
+    a_bits, a = bf16(rng, (M, Ka))
+    b_bits, b = bf16(rng, (N, Kd), 0.5)
+    A = torch.from_numpy(a_bits.view(np.int16)).to(DEV)
+    B = torch.from_numpy(b_bits.view(np.int16)).to(DEV)
+    parts = gpu_ctx.gemm_bf16_ex(A, B, config, splits, scale=2.0)
+    torch.cuda.synchronize()
+    a_rep = np.concatenate([a] * (Kd // Ka), axis=1)
+    kb = Kd // 64
+    total = np.zeros((N, M))
+    for z in range(splits):
+        k0, k1 = 64 * (z * kb // splits), 64 * ((z + 1) * kb // splits)
+        exact = 2.0 * (b[:, k0:k1] @ a_rep[:, k0:k1].T)
+        bound = (k1 - k0) * 2.0 ** -23 * 2.0 * (np.abs(b[:, k0:k1]) @ np.abs(a_rep[:, k0:k1]).T) + 1e-30
+        got = parts[z].double().cpu().numpy()
+        assert np.all(np.abs(got - exact) <= bound), (z, (np.abs(got - exact) / bound).max())
+        total += got
+    exact = 2.0 * (b @ a_rep.T)
+    bound = (Kd + splits) * 2.0 ** -23 * 2.0 * (np.abs(b) @ np.abs(a_rep).T) + 1e-30
+    assert np.all(np.abs(total - exact) <= bound)
+
+
+def test_gemm_ex_rejects_bad_config(gpu_ctx):
+    A = torch.zeros(128, 128, dtype=torch.int16, device=DEV)
+    B = torch.zeros(128, 128, dtype=torch.int16, device=DEV)
+    for cfg, spl in [(-1, 1), (4, 1), (0, 0), (0, 3)]:          # Kd / 64 = 2 parts at most
+        with pytest.raises(pkg.Gpl1Error) as e:
+            gpu_ctx.gemm_bf16_ex(A, B, cfg, spl)
+        assert e.value.status == 1

@@ -43,6 +43,11 @@ def test_shared_k_vs_oracle(gpu_ctx, n, p, nrhs, k):
         assert np.abs(Xh[b]).sum() <= rho[b] * (1 + 1e-6)
     others = [r for b, r in enumerate(res) if b not in check]
     assert all(r.status in (0, 3, 4) and r.iters > 0 for r in others)
+    # the autotuner recorded both products of this shape (the second may be split)
+    tuned = {t["shape"][:4]: t for t in gpu_ctx.gemm_tuned()}
+    g1, g2 = tuned[(p, nrhs, 3 * n, n)], tuned[(n, nrhs, 3 * p, p)]
+    assert g1["splits"] == 1 and 0 <= g1["config"] < 4 and g1["ms"] > 0
+    assert 1 <= g2["splits"] <= min(8, 3 * p // 64 // 8) and 0 <= g2["config"] < 4 and g2["ms"] > 0
 
 
 def test_shared_k_first_iterations_match_single_solver(gpu_ctx):
@@ -65,6 +70,11 @@ def test_shared_k_first_iterations_match_single_solver(gpu_ctx):
 def test_shared_k_rejects_unsupported_shapes(gpu_ctx):
     K = torch.zeros(100, 256, dtype=torch.int16, device=DEV)
     Y = torch.zeros(2, 100, dtype=torch.float32, device=DEV)
+    with pytest.raises(pkg.Gpl1Error) as e:
+        gpu_ctx.solve_shared_k(K, Y, [1.0, 1.0])
+    assert e.value.status == 7
+    K = torch.zeros(4352, 256, dtype=torch.int16, device=DEV)     # n > 4320 rows
+    Y = torch.zeros(2, 4352, dtype=torch.float32, device=DEV)
     with pytest.raises(pkg.Gpl1Error) as e:
         gpu_ctx.solve_shared_k(K, Y, [1.0, 1.0])
     assert e.value.status == 7
