@@ -202,12 +202,13 @@ def objective_f64(prob, x) -> float:
 
 
 # ------------------------------------------------- batched ragged form (c3a)
-def run_batched(count, steps, dev):
+def run_batched(count, steps, dev, plain_sample=64):
     """Solves/s of `count` instances of the ragged recipe (n in [128, 2048], p = 4n,
-    BF16 K, +-1 signals): one persistent gpl1_solve_batched launch per step, and the
-    same instances solved one after another with gpl1_solve (the plain form).  Each
-    instance stops at relative gap 1e-6 against the oracle's optimum of that instance
-    (tests/golden/c3a_fstar.json, written by tests/golden/make_golden.py)."""
+    BF16 K, +-1 signals): one persistent gpl1_solve_batched launch per step, the same
+    launch replayed from its CUDA graph (gpl1_plan_run), and a sample of the instances
+    (every count/plain_sample-th) solved one after another with gpl1_solve (the plain
+    form).  Each instance stops at relative gap 1e-6 against the oracle's optimum of
+    that instance (tests/golden/c3a_fstar.json, written by tests/golden/make_golden.py)."""
     import torch
 
     import paper_0902_4424_gb300 as pkg
@@ -243,16 +244,31 @@ def run_batched(count, steps, dev):
     ok = sum(r.status == 0 for r in res)
     iters = [r.iters for r in res]
     algo = sum(it * 2.0 * pr.n * pr.p * 2 for it, pr in zip(iters, probs))
-    # the plain form: the same instances one after another, each its own cooperative launch
+    # the same batched solve as a CUDA graph (no host work per replay)
+    plan = ctx.plan_batched(descs, pkg.BF16, prm)
+    plan.run()
+    torch.cuda.synchronize()
+    gms = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.run()
+        b.record(stream)
+        b.synchronize()
+        gms.append(a.elapsed_time(b))
+    plan.close()
+    # the plain form on a sample: one instance after another, each its own cooperative launch
+    pick = list(range(0, count, max(1, count // plain_sample)))[:plain_sample]
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     plain_ok = 0
-    for (K, y, x), pr, fs in zip(keep, probs, fstars):
-        _, r = ctx.solve(K, y, pr.rho, x=x, p=pr.p, params=prm, f_star=fs)
+    for q in pick:
+        K, y, x = keep[q]
+        _, r = ctx.solve(K, y, probs[q].rho, x=x, p=probs[q].p, params=prm, f_star=fstars[q])
         plain_ok += r.status == 0
     b.record(stream)
     b.synchronize()
-    plain_ms = a.elapsed_time(b)
+    plain_ms = a.elapsed_time(b) * count / len(pick)   # the whole set at the sample's rate
     # untimed: the oracle's optimum on a few instances, against the batched x
     ctx.solve_batched(descs, pkg.BF16, prm)
     torch.cuda.synchronize()
@@ -262,7 +278,8 @@ def run_batched(count, steps, dev):
     mean_ms = statistics.mean(ms)
     out = {"workload": f"c3a_ragged{count}_bf16", "instances": count, "solves_per_s": count / (mean_ms / 1e3),
            "ms_per_batch": mean_ms, "ok": ok, "iters_mean": statistics.mean(iters), "iters_max": max(iters),
-           "plain_solves_per_s": count / (plain_ms / 1e3), "plain_ok": plain_ok,
+           "graph_solves_per_s": count / (statistics.mean(gms) / 1e3),
+           "plain_solves_per_s": count / (plain_ms / 1e3), "plain_sample": len(pick), "plain_ok": plain_ok,
            "speedup_vs_plain": plain_ms / mean_ms, "stop": f"kernel stop rel_gap<={0.5 * TOL:g} vs oracle f* per instance",
            "verified_max_rel_gap": max(gaps) if gaps else None, "verified_instances": len(gaps),
            "hbm_gbs": algo / (statistics.mean(kms) / 1e3) / 1e9}
@@ -589,7 +606,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batched-sample", type=int, default=64,
+    ap.add_argument("--batched-sample", type=int, default=512,
                     help="also time this many ragged instances batched vs plain (0: skip)")
     ap.add_argument("--shared-k", type=int, default=1024,
                     help="also time this many right-hand sides on one shared K (0: skip)")

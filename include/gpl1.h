@@ -174,6 +174,27 @@ gpl1_status gpl1_solve(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype k_dty
 gpl1_status gpl1_solve_batched(gpl1_ctx* ctx, const gpl1_problem* probs, int count,
                                gpl1_dtype k_dtype, const gpl1_params* prm, gpl1_result* res);
 
+/* Batched plans: repeated solves of the same instances without host work.
+ * gpl1_plan_create checks the instances and parameters as gpl1_solve_batched
+ * does, lays out a workspace owned by the plan, encodes the tensor maps,
+ * orders the queue (largest n p first), and records everything one batched
+ * solve enqueues (zeroing x when prm->x0_is_zero, zeroing the accumulation
+ * buffers, the upload of the descriptors, the persistent launch, the read-back
+ * of the results into pinned memory) as a CUDA graph.  gpl1_plan_run replays
+ * the graph on the context's stream, synchronises, and fills res (host array
+ * of `count` results, in the order of probs) with the same values
+ * gpl1_solve_batched gives.  The instances' device arrays (K, y, x) must stay
+ * allocated while the plan lives; their contents may change between runs
+ * (new right-hand sides written into y, new K values); rho, f_star, the
+ * sizes, the dtype and the parameters are fixed at creation.  A plan belongs
+ * to its context: destroy it first.  Errors: as gpl1_solve_batched;
+ * GPL1_ERR_CUDA if the capture or the graph fails. */
+typedef struct gpl1_plan gpl1_plan;
+gpl1_status gpl1_plan_create(gpl1_ctx* ctx, const gpl1_problem* probs, int count, gpl1_dtype k_dtype,
+                             const gpl1_params* prm, gpl1_plan** out);
+gpl1_status gpl1_plan_run(gpl1_plan* plan, gpl1_result* res);
+void gpl1_plan_destroy(gpl1_plan* plan);
+
 /* Tensor-core product used by the shared-K form of the method (many
  * right-hand sides on one K turn K^T r and K d into matrix products):
  *   out[n * ldo + m] = scale * sum_{k < Kd} A[m * lda + (k mod Ka)] * B[n * ldb + k]

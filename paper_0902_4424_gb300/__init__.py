@@ -31,7 +31,7 @@ ALGORITHMIC = (0, 3, 4, 5, 6)
 EXPORTS = ["gpl1_create", "gpl1_destroy", "gpl1_set_stream", "gpl1_last_error", "gpl1_params_default",
            "gpl1_project", "gpl1_solve", "gpl1_solve_batched", "gpl1_solve_noalloc", "gpl1_gemm_bf16",
            "gpl1_gemm_bf16_ex", "gpl1_gemm_tuned", "gpl1_solve_shared_k", "gpl1_lista_forward",
-           "gpl1_lista_grad", "gpl1_lista_train"]
+           "gpl1_lista_grad", "gpl1_lista_train", "gpl1_plan_create", "gpl1_plan_run", "gpl1_plan_destroy"]
 
 
 class Gpl1Error(RuntimeError):
@@ -95,6 +95,11 @@ def lib():
         L.gpl1_gemm_bf16.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_float]
+        L.gpl1_plan_create.argtypes = [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]
+        L.gpl1_plan_run.argtypes = [ctypes.c_void_p, ctypes.POINTER(Result)]
+        L.gpl1_plan_destroy.argtypes = [ctypes.c_void_p]
+        L.gpl1_plan_destroy.restype = None
         L.gpl1_gemm_bf16_ex.argtypes = L.gpl1_gemm_bf16.argtypes + [ctypes.c_int, ctypes.c_int, ctypes.c_longlong]
         L.gpl1_gemm_tuned.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -348,6 +353,18 @@ class Context:
             self._check(st)
         return X, list(res)
 
+    def plan_batched(self, problems: Sequence[Problem], dtype: int, params: Params | None = None):
+        """gpl1_plan_create: the batched solve of these instances recorded once as a CUDA
+        graph; BatchedPlan.run() replays it.  The tensors behind the descriptors must outlive
+        the plan (their contents may change between runs)."""
+        count = len(problems)
+        arr = (Problem * count)(*problems)
+        prm = params_default() if params is None else params
+        h = ctypes.c_void_p()
+        self._bind_stream()
+        self._check(lib().gpl1_plan_create(self._h, arr, count, dtype, ctypes.byref(prm), ctypes.byref(h)))
+        return BatchedPlan(self, h, count)
+
     def solve_batched(self, problems: Sequence[Problem], dtype: int, params: Params | None = None):
         """Solve independent instances in one persistent launch (gpl1_solve_batched); returns results."""
         count = len(problems)
@@ -359,6 +376,33 @@ class Context:
         if st not in ALGORITHMIC:
             self._check(st)
         return list(res)
+
+
+class BatchedPlan:
+    """A batched solve recorded as a CUDA graph (gpl1_plan_*); run() replays it."""
+
+    def __init__(self, ctx: "Context", handle, count: int):
+        self._ctx, self._h, self.count = ctx, handle, count
+
+    def run(self):
+        """Replay on the context's stream (bound to PyTorch's current stream); returns the results."""
+        res = (Result * self.count)()
+        self._ctx._bind_stream()
+        st = lib().gpl1_plan_run(self._h, res)
+        if st not in ALGORITHMIC:
+            self._ctx._check(st)
+        return list(res)
+
+    def close(self):
+        if self._h:
+            lib().gpl1_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 NOALLOC_SCRATCH_BYTES = 4 << 20

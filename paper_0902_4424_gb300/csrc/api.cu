@@ -273,54 +273,61 @@ namespace {
 
 // Launch `count` instances.  group > 1: one instance over `group` CTAs
 // (cooperative); group == 1: persistent CTAs pulling instances from a queue.
-gpl1_status run(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
-                gpl1_result* res) {
-  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-  // largest-first order for the queue (the longest instances start first)
-  std::vector<int> order(count);
-  std::iota(order.begin(), order.end(), 0);
+// Workspace layout of one launch of `count` instances:
+// [counters 256][descs][results][tmaps][gbuf/kbuf/pbuf per instance].
+struct BatchLayout {
+  std::vector<int> order;   // queue order: largest n p first (the longest instances start first)
+  size_t off_desc = 256, off_res = 0, off_tmap = 0, off_bufs = 0, total = 0;
+  std::vector<size_t> off_g, off_k, off_p;
+  bool batched = false;
+};
+
+BatchLayout batch_layout(const gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt) {
+  BatchLayout L;
+  L.order.resize(count);
+  std::iota(L.order.begin(), L.order.end(), 0);
   if (count > 1)
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    std::stable_sort(L.order.begin(), L.order.end(), [&](int a, int b) {
       return probs[a].n * probs[a].p > probs[b].n * probs[b].p;
     });
   const int as = acc_size(dt);
-  // workspace: [counters 256][descs][results][tmaps][gbuf/kbuf per instance]
-  const size_t off_desc = 256;
-  const size_t off_res = align_up(off_desc + sizeof(InstDesc) * count, 256);
-  const size_t off_tmap = align_up(off_res + sizeof(gpl1_result) * count, 256);
-  const bool batched = count > 1;
-  size_t off_bufs = align_up(off_tmap + (batched ? sizeof(CUtensorMap) * count : 0), 256);
-  std::vector<size_t> off_g(count), off_k(count), off_p(count);
-  const int max_group = batched ? 1 : ctx->num_sms * 4;
-  size_t cur = off_bufs;
+  L.batched = count > 1;
+  L.off_res = align_up(L.off_desc + sizeof(InstDesc) * count, 256);
+  L.off_tmap = align_up(L.off_res + sizeof(gpl1_result) * count, 256);
+  L.off_bufs = align_up(L.off_tmap + (L.batched ? sizeof(CUtensorMap) * count : 0), 256);
+  L.off_g.resize(count);
+  L.off_k.resize(count);
+  L.off_p.resize(count);
+  const int max_group = L.batched ? 1 : ctx->num_sms * 4;
+  size_t cur = L.off_bufs;
   for (int q = 0; q < count; ++q) {
-    const Sizes s = sizes_of(&probs[q], dt);
-    off_g[q] = cur;
-    cur = align_up(cur + 3 * s.pp * as, 256);
-    off_k[q] = cur;
-    cur = align_up(cur + 2 * kbuf_stride(s.nn, as), 256);
-    off_p[q] = cur;   // pass-B partials: 4 doubles per CTA of the group
+    const Sizes sz = sizes_of(&probs[q], dt);
+    L.off_g[q] = cur;
+    cur = align_up(cur + 3 * sz.pp * as, 256);
+    L.off_k[q] = cur;
+    cur = align_up(cur + 2 * kbuf_stride(sz.nn, as), 256);
+    L.off_p[q] = cur;   // pass-B partials: 4 doubles per CTA of the group
     cur = align_up(cur + 32 * static_cast<size_t>(max_group), 256);
   }
-  gpl1_status st = ensure_ws(ctx, cur);
-  if (st) return st;
-  st = ensure_host_res(ctx, count);
-  if (st) return st;
-  uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
+  L.total = cur;
+  return L;
+}
 
-  // host staging of descriptors and tensor maps
-  ctx->host_stage.assign(off_bufs - off_desc, 0);
-  InstDesc* hd = reinterpret_cast<InstDesc*>(ctx->host_stage.data());
-  CUtensorMap* ht = reinterpret_cast<CUtensorMap*>(ctx->host_stage.data() + (off_tmap - off_desc));
-  gpl1_result* hr = reinterpret_cast<gpl1_result*>(ctx->host_stage.data() + (off_res - off_desc));
+// Host image of [descs][results][tmaps] (off_bufs - off_desc bytes at `host`)
+// for a workspace at `ws`; the single solve's tensor map goes to *tmap0.
+gpl1_status stage_batch(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
+                        const BatchLayout& L, uint8_t* ws, uint8_t* host, CUtensorMap* tmap0) {
+  std::memset(host, 0, L.off_bufs - L.off_desc);
+  InstDesc* hd = reinterpret_cast<InstDesc*>(host);
+  CUtensorMap* ht = reinterpret_cast<CUtensorMap*>(host + (L.off_tmap - L.off_desc));
+  gpl1_result* hr = reinterpret_cast<gpl1_result*>(host + (L.off_res - L.off_desc));
   for (int q = 0; q < count; ++q) {   // overwritten by the kernel; stays if an instance never ran
     hr[q].status = GPL1_ERR_TIMEOUT;
     hr[q].stop = GPL1_STOP_ERROR;
   }
-  CUtensorMap tmap0;
-  std::memset(&tmap0, 0, sizeof tmap0);
+  std::memset(tmap0, 0, sizeof *tmap0);
   for (int q = 0; q < count; ++q) {
-    const int src = order[q];
+    const int src = L.order[q];
     const gpl1_problem& pr = probs[src];
     InstDesc& d = hd[q];
     d.y = pr.y;
@@ -331,40 +338,49 @@ gpl1_status run(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, con
     d.p = static_cast<int>(pr.p);
     d.x0_zero = prm->x0_is_zero ? 1 : 0;
     d.pad = 0;
-    d.gbuf = ws + off_g[src];
-    d.kbuf = ws + off_k[src];
-    d.res = reinterpret_cast<gpl1_result*>(ws + off_res) + src;
+    d.gbuf = ws + L.off_g[src];
+    d.kbuf = ws + L.off_k[src];
+    d.res = reinterpret_cast<gpl1_result*>(ws + L.off_res) + src;
     d.trace = pr.trace;
     d.trace_cap = pr.trace ? pr.trace_cap : 0;
-    d.pbuf = ws + off_p[src];
-    if (batched) {
+    d.pbuf = ws + L.off_p[src];
+    gpl1_status st;
+    if (L.batched) {
       st = encode_tmap(ctx, &ht[q], &pr, dt);
-      d.tmap = ws + off_tmap + sizeof(CUtensorMap) * q;
+      d.tmap = ws + L.off_tmap + sizeof(CUtensorMap) * q;
     } else {
-      st = encode_tmap(ctx, &tmap0, &pr, dt);
+      st = encode_tmap(ctx, tmap0, &pr, dt);
       d.tmap = nullptr;
     }
     if (st) return st;
   }
+  return GPL1_OK;
+}
+
+// Everything one solve puts on `stream`: zero x (x0 = 0), the counters and the
+// accumulation buffers, upload the host image, launch, read the results back
+// into host_res.  No host synchronisation, so a stream capture can record it.
+gpl1_status enqueue_batch(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
+                          const BatchLayout& L, uint8_t* ws, const uint8_t* host, const CUtensorMap& tmap0,
+                          cudaStream_t stream, gpl1_result* host_res, cudaEvent_t ev0, cudaEvent_t ev1,
+                          bool capture = false) {
+  // under stream capture the events become event-record nodes of the graph
+  const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (prm->x0_is_zero)   // x0 = 0: the iterate buffer must start at zero
     for (int q = 0; q < count; ++q)
-      GPL1_CUDA(cudaMemsetAsync(probs[q].x, 0, static_cast<size_t>(probs[q].p) * (dt == GPL1_F64 ? 8 : 4),
-                                ctx->stream),
+      GPL1_CUDA(cudaMemsetAsync(probs[q].x, 0, static_cast<size_t>(probs[q].p) * (dt == GPL1_F64 ? 8 : 4), stream),
                 "cudaMemsetAsync(x)");
-  GPL1_CUDA(cudaMemsetAsync(ws, 0, 256, ctx->stream), "cudaMemsetAsync");
-  GPL1_CUDA(cudaMemsetAsync(ws + off_bufs, 0, cur - off_bufs, ctx->stream), "cudaMemsetAsync");
-  GPL1_CUDA(cudaMemcpyAsync(ws + off_desc, ctx->host_stage.data(), off_bufs - off_desc, cudaMemcpyHostToDevice,
-                            ctx->stream),
+  GPL1_CUDA(cudaMemsetAsync(ws, 0, 256, stream), "cudaMemsetAsync");
+  GPL1_CUDA(cudaMemsetAsync(ws + L.off_bufs, 0, L.total - L.off_bufs, stream), "cudaMemsetAsync");
+  GPL1_CUDA(cudaMemcpyAsync(ws + L.off_desc, host, L.off_bufs - L.off_desc, cudaMemcpyHostToDevice, stream),
             "cudaMemcpyAsync(desc)");
-
   KArgs ka;
-  ka.desc = reinterpret_cast<const InstDesc*>(ws + off_desc);
+  ka.desc = reinterpret_cast<const InstDesc*>(ws + L.off_desc);
   ka.count = count;
   ka.queue = reinterpret_cast<unsigned*>(ws + 0);
   ka.bar = reinterpret_cast<unsigned*>(ws + 64);
   ka.err = reinterpret_cast<int*>(ws + 128);
   ka.prm = to_kernel_params(prm);
-
   int occ = 0;
   GPL1_CUDA(cudaFuncSetAttribute(gpss_kernel_ptr(dt), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(gpss_smem_bytes(dt))),
@@ -372,35 +388,59 @@ gpl1_status run(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, con
   GPL1_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gpss_kernel_ptr(dt), kThreads, gpss_smem_bytes(dt)),
             "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (occ < 1) return fail(ctx, GPL1_ERR_CUDA, "solver kernel does not fit on an SM");
-  if (!ctx->ev[0]) {
-    GPL1_CUDA(cudaEventCreate(&ctx->ev[0]), "cudaEventCreate");
-    GPL1_CUDA(cudaEventCreate(&ctx->ev[1]), "cudaEventCreate");
-  }
-  GPL1_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream), "cudaEventRecord");
-  if (!batched) {
-    const Sizes s = sizes_of(&probs[0], dt);
-    const long long G = std::min<long long>(static_cast<long long>(ctx->num_sms) * occ, s.units);
+  GPL1_CUDA(cudaEventRecordWithFlags(ev0, stream, evf), "cudaEventRecord");
+  if (!L.batched) {
+    const Sizes sz = sizes_of(&probs[0], dt);
+    const long long G = std::min<long long>(static_cast<long long>(ctx->num_sms) * occ, sz.units);
     ka.group = static_cast<int>(G);
-    GPL1_CUDA(launch_gpss(dt, ka, tmap0, ka.group, G > 1, ctx->stream), "solver launch");
+    GPL1_CUDA(launch_gpss(dt, ka, tmap0, ka.group, G > 1, stream), "solver launch");
   } else {
     ka.group = 1;
     const int grid = std::min(ctx->num_sms * occ, count);
-    GPL1_CUDA(launch_gpss(dt, ka, tmap0, grid, false, ctx->stream), "solver launch");
+    GPL1_CUDA(launch_gpss(dt, ka, tmap0, grid, false, stream), "solver launch");
   }
-  GPL1_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream), "cudaEventRecord");
-  GPL1_CUDA(cudaMemcpyAsync(ctx->host_res, ws + off_res, sizeof(gpl1_result) * count, cudaMemcpyDeviceToHost,
-                            ctx->stream),
+  GPL1_CUDA(cudaEventRecordWithFlags(ev1, stream, evf), "cudaEventRecord");
+  GPL1_CUDA(cudaMemcpyAsync(host_res, ws + L.off_res, sizeof(gpl1_result) * count, cudaMemcpyDeviceToHost, stream),
             "cudaMemcpyAsync(result)");
-  GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "solver");
-  std::memcpy(res, ctx->host_res, sizeof(gpl1_result) * count);
+  return GPL1_OK;
+}
+
+// After the stream has synchronised: results out, kernel time, worst status.
+gpl1_status finish_batch(gpl1_ctx* ctx, int count, const gpl1_result* host_res, gpl1_result* res, cudaEvent_t ev0,
+                         cudaEvent_t ev1) {
+  std::memcpy(res, host_res, sizeof(gpl1_result) * count);
   float ms = 0.f;
-  GPL1_CUDA(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]), "cudaEventElapsedTime");
+  GPL1_CUDA(cudaEventElapsedTime(&ms, ev0, ev1), "cudaEventElapsedTime");
   for (int q = 0; q < count; ++q) res[q].kernel_ms = ms;
   int worst = GPL1_OK;
   for (int q = 0; q < count; ++q)
     if (res[q].status != GPL1_OK && res[q].status != GPL1_ERR_NOT_CONVERGED) worst = res[q].status;
   if (worst != GPL1_OK) return fail(ctx, static_cast<gpl1_status>(worst), "an instance failed (status %d)", worst);
   return GPL1_OK;
+}
+
+gpl1_status run(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
+                gpl1_result* res) {
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const BatchLayout L = batch_layout(ctx, probs, count, dt);
+  gpl1_status st = ensure_ws(ctx, L.total);
+  if (st) return st;
+  st = ensure_host_res(ctx, count);
+  if (st) return st;
+  uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
+  ctx->host_stage.assign(L.off_bufs - L.off_desc, 0);
+  CUtensorMap tmap0;
+  st = stage_batch(ctx, probs, count, dt, prm, L, ws, ctx->host_stage.data(), &tmap0);
+  if (st) return st;
+  if (!ctx->ev[0]) {
+    GPL1_CUDA(cudaEventCreate(&ctx->ev[0]), "cudaEventCreate");
+    GPL1_CUDA(cudaEventCreate(&ctx->ev[1]), "cudaEventCreate");
+  }
+  st = enqueue_batch(ctx, probs, count, dt, prm, L, ws, ctx->host_stage.data(), tmap0, ctx->stream, ctx->host_res,
+                     ctx->ev[0], ctx->ev[1]);
+  if (st) return st;
+  GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "solver");
+  return finish_batch(ctx, count, ctx->host_res, res, ctx->ev[0], ctx->ev[1]);
 }
 
 }  // namespace
@@ -432,6 +472,103 @@ gpl1_status gpl1_solve_batched(gpl1_ctx* ctx, const gpl1_problem* probs, int cou
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched plans: the enqueue of gpl1_solve_batched captured once into a CUDA
+// graph and replayed (declaration and contract in gpl1.h).
+
+struct gpl1_plan {
+  gpl1_ctx* ctx = nullptr;
+  int device = 0;
+  int count = 0, dt = 0;
+  gpl1_params prm{};
+  std::vector<gpl1_problem> probs;
+  BatchLayout layout;
+  void* ws = nullptr;                 // the plan's own workspace
+  uint8_t* host_img = nullptr;        // pinned: descriptors, initial results, tensor maps
+  gpl1_result* host_res = nullptr;    // pinned: results read back by the graph
+  CUtensorMap tmap0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" void gpl1_plan_destroy(gpl1_plan* pl) {
+  if (!pl) return;
+  cudaSetDevice(pl->device);
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  for (cudaEvent_t e : pl->ev)
+    if (e) cudaEventDestroy(e);
+  if (pl->ws) cudaFree(pl->ws);
+  if (pl->host_img) cudaFreeHost(pl->host_img);
+  if (pl->host_res) cudaFreeHost(pl->host_res);
+  delete pl;
+}
+
+extern "C" gpl1_status gpl1_plan_create(gpl1_ctx* ctx, const gpl1_problem* probs, int count, gpl1_dtype dt,
+                                        const gpl1_params* prm, gpl1_plan** out) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  if (!out) return fail(ctx, GPL1_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (dt != GPL1_F64 && dt != GPL1_F32 && dt != GPL1_BF16) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad dtype");
+  if (!probs || count < 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "need probs and count >= 1");
+  gpl1_status st = check_params(ctx, prm);
+  if (st) return st;
+  for (int q = 0; q < count; ++q) {
+    st = check_problem(ctx, &probs[q], dt, q);
+    if (st) return st;
+  }
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  gpl1_plan* pl = new gpl1_plan;
+  pl->ctx = ctx;
+  pl->device = ctx->device;
+  pl->count = count;
+  pl->dt = dt;
+  pl->prm = *prm;
+  pl->probs.assign(probs, probs + count);
+  pl->layout = batch_layout(ctx, probs, count, dt);
+  const BatchLayout& L = pl->layout;
+  cudaStream_t cap = nullptr;
+  auto bail = [&](gpl1_status code) {
+    if (cap) cudaStreamDestroy(cap);
+    gpl1_plan_destroy(pl);
+    return code;
+  };
+  cudaError_t e = cudaMalloc(&pl->ws, L.total);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&pl->host_img), L.off_bufs - L.off_desc);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&pl->host_res), sizeof(gpl1_result) * count);
+  if (e == cudaSuccess) e = cudaEventCreate(&pl->ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&pl->ev[1]);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "plan allocation"));
+  st = stage_batch(ctx, probs, count, dt, prm, L, static_cast<uint8_t*>(pl->ws), pl->host_img, &pl->tmap0);
+  if (st) return bail(st);
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaStreamBeginCapture"));
+  st = enqueue_batch(ctx, pl->probs.data(), count, dt, &pl->prm, L, static_cast<uint8_t*>(pl->ws), pl->host_img,
+                     pl->tmap0, cap, pl->host_res, pl->ev[0], pl->ev[1], true);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(cap, &g);
+  pl->graph = g;
+  if (st) return bail(st);
+  if (ee != cudaSuccess) return bail(cuda_fail(ctx, ee, "cudaStreamEndCapture"));
+  e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+  if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "cudaGraphInstantiate"));
+  cudaStreamDestroy(cap);
+  *out = pl;
+  return GPL1_OK;
+}
+
+extern "C" gpl1_status gpl1_plan_run(gpl1_plan* pl, gpl1_result* res) {
+  if (!pl) return GPL1_ERR_INVALID_ARG;
+  gpl1_ctx* ctx = pl->ctx;
+  if (!res) return fail(ctx, GPL1_ERR_INVALID_ARG, "res is NULL");
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  GPL1_CUDA(cudaGraphLaunch(pl->exec, ctx->stream), "cudaGraphLaunch");
+  GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "plan");
+  return finish_batch(ctx, pl->count, pl->host_res, res, pl->ev[0], pl->ev[1]);
+}
 
 // ---------------------------------------------------------------------------
 // gpl1_solve_noalloc: gpl1_solve with its workspace in a fixed static device

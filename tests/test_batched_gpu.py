@@ -68,3 +68,40 @@ def test_ragged_batch_config3_shapes(gpu_ctx):
         assert r.status == 0 and r.stop == 0, (pr.n, r.as_dict(), gap)
         assert gap <= 1e-6
         assert np.abs(x).sum() <= pr.rho * (1 + 1e-6)
+
+
+def test_batched_plan_replays_the_batched_solve(gpu_ctx):
+    """gpl1_plan_*: the batched solve recorded as a CUDA graph gives, on every replay,
+    the iterates and results of gpl1_solve_batched (the same kernel on the same
+    instances), and follows right-hand sides rewritten in place between replays."""
+    rng = np.random.default_rng(5)
+    sizes = [int(v) for v in rng.integers(32, 300, size=12)]
+    probs = [W.gaussian(n, 4 * n, max(1, n // 20), dtype=W.DT_F32, seed=2000 + i, law="pm1")
+             for i, n in enumerate(sizes)]
+    keep = [upload(pr) for pr in probs]
+    descs = [pkg.Context.make_problem(K, y, pr.rho, x, pr.p) for (K, y, x), pr in zip(keep, probs)]
+    prm = pkg.params_default(stop_rule=0, x0_is_zero=1, max_iter=40)
+    ref = gpu_ctx.solve_batched(descs, W.DT_F32, prm)
+    torch.cuda.synchronize()
+    x_ref = [x.clone() for _, _, x in keep]
+    plan = gpu_ctx.plan_batched(descs, W.DT_F32, prm)
+    for _ in range(2):
+        for _, _, x in keep:
+            x.fill_(7.0)                                 # x0 = 0 is re-established by the graph
+        res = plan.run()
+        torch.cuda.synchronize()
+        for (_, _, x), xr, r, rr in zip(keep, x_ref, res, ref):
+            assert torch.equal(x, xr)
+            assert (r.status, r.iters, r.f, r.backtracks) == (rr.status, rr.iters, rr.f, rr.backtracks)
+    # new right-hand sides in place: the replay solves them
+    for (_, y, _), pr in zip(keep, probs):
+        y.mul_(0.5)
+    res = plan.run()
+    torch.cuda.synchronize()
+    x_new = [x.clone() for _, _, x in keep]
+    ref2 = gpu_ctx.solve_batched(descs, W.DT_F32, prm)
+    torch.cuda.synchronize()
+    for (_, _, x), xn, r, rr in zip(keep, x_new, res, ref2):
+        assert torch.equal(x, xn)
+        assert (r.status, r.iters, r.f) == (rr.status, rr.iters, rr.f)
+    plan.close()
