@@ -359,25 +359,30 @@ def run_shared_k(nrhs, dev, verify=16, plain=8):
 
 
 # ------------------------------------------------ learned warm start (c4)
-def run_warm_start(dev, steps=600, batch=256):
-    """The learned warm start on K 1024 x 4096 (BF16): training targets are the
-    solver's own solutions of the training samples (shared-K form), the network
-    (6 layers, W_l initialised to K^T / ||K||^2, theta_l to the median lambda /
-    ||K||^2) is trained with Adam on the GPU, and the test samples are solved to
-    relative gap 1e-6 (kernel stop 5e-7, stored oracle optima) from x0 = 0 (cold)
-    and from the projected network output (warm, inference included)."""
+def run_warm_start(dev, steps=3000, batch=256, ntrain=65536, lr=3e-4):
+    """The learned warm start on K 1024 x 4096 (BF16): `ntrain` training right-hand
+    sides (workloads.warm_start_train) with the solver's own solutions as targets
+    (shared-K form), the network (6 layers, W_l initialised to K^T / ||K||^2,
+    theta_l to the median lambda / ||K||^2) trained with Adam on the GPU, and the
+    test samples solved to relative gap 1e-6 (kernel stop 5e-7, stored oracle
+    optima) from x0 = 0 (cold) and from the projected network output (warm,
+    inference included; alpha_0 from the projected-gradient step at x0, rule 1)."""
     import torch
 
     import paper_0902_4424_gb300 as pkg
     import workloads as W
     with open(os.path.join(ROOT, "tests", "golden", "c4_fstar.json")) as fh:
         gold = json.load(fh)
-    Ks, ldk, Y, rho, Xt, ntr = W.warm_start_split()
+    Ks, ldk, Y, rho, Xt, ntr0 = W.warm_start_split()
     n, p = Ks.shape[0], Xt.shape[1]
-    nte = Y.shape[0] - ntr
+    nte = Y.shape[0] - ntr0
     fstars = gold["f_star"]
+    Ytr, rho_tr = W.warm_start_train(ntrain, n, p)
     K = torch.from_numpy(Ks.view(np.int16)).to(dev)
-    Yd = torch.from_numpy(np.ascontiguousarray(Y)).to(dev)
+    # training samples first, then the test samples (the last rows of the split)
+    Yd = torch.from_numpy(np.ascontiguousarray(np.concatenate([Ytr, Y[ntr0:]]))).to(dev)
+    rho = np.concatenate([rho_tr, rho[ntr0:]])
+    ntr = ntrain
     ctx = pkg.Context(dev.index or 0)
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
@@ -404,7 +409,7 @@ def run_warm_start(dev, steps=600, batch=256):
     v = torch.zeros_like(m)
     a, b = ev(), ev()
     a.record(stream)
-    losses = ctx.lista_train(K, Wd, thd, m, v, Yd[:ntr], Xtr, batch=batch, steps=steps, lr=1e-4, lr_theta=1e-4)
+    losses = ctx.lista_train(K, Wd, thd, m, v, Yd[:ntr], Xtr, batch=batch, steps=steps, lr=lr, lr_theta=lr)
     b.record(stream)
     b.synchronize()
     train_ms = a.elapsed_time(b)
@@ -418,14 +423,18 @@ def run_warm_start(dev, steps=600, batch=256):
     b.record(stream)
     b.synchronize()
     cold_ms = a.elapsed_time(b)
+    prm_w = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=0.5 * TOL, max_iter=5000, alpha0_rule=1)
     a, b = ev(), ev()
     a.record(stream)
     X0 = ctx.lista_forward(K, Wd, thd, Yte)
-    Xw, rw = ctx.solve_shared_k(K, Yte, rho[ntr:], p=p, f_star=fstars, params=prm, X=X0)
+    Xw, rw = ctx.solve_shared_k(K, Yte, rho[ntr:], p=p, f_star=fstars, params=prm_w, X=X0)
     b.record(stream)
     b.synchronize()
     warm_ms = a.elapsed_time(b)
-    probs = [W.Problem(Ks, n, p, ldk, W.DT_BF16, Y[ntr + q].copy(), float(rho[ntr + q]), Xt[ntr + q], "c4")
+    # the network's output (the solve above overwrote X0) against the solutions, on the test samples
+    Xn = ctx.lista_forward(K, Wd, thd, Yte)
+    test_rel_err = float((((Xn - Xc) ** 2).sum(1).mean() / (Xc ** 2).sum(1).mean()).sqrt().item())
+    probs = [W.Problem(Ks, n, p, ldk, W.DT_BF16, Y[ntr0 + q].copy(), float(rho[ntr + q]), Xt[ntr0 + q], "c4")
              for q in range(nte)]
     Xwh = Xw.double().cpu().numpy()
     idx = np.linspace(0, nte - 1, 16).astype(int)
@@ -435,6 +444,7 @@ def run_warm_start(dev, steps=600, batch=256):
             "layers": layers, "train_steps": steps, "batch": batch, "train_ms": train_ms,
             "target_solve_ms": target_ms, "loss_first": float(np.mean(losses[:8])),
             "loss_last": float(np.mean(losses[-8:])),
+            "test_rel_err": test_rel_err,
             "cold_solves_per_s": nte / (cold_ms / 1e3), "warm_solves_per_s": nte / (warm_ms / 1e3),
             "cold_iters_mean": statistics.mean(r.iters for r in rc),
             "warm_iters_mean": statistics.mean(r.iters for r in rw),

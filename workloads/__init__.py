@@ -210,3 +210,29 @@ def warm_start_split():
     """(K, ldk, Y, rho, X_true, ntrain): the measured warm-start workload, K 1024 x 4096."""
     Ks, ldk, Y, rho, X = warm_start_data(1024, 4096, WARM_TRAIN + WARM_TEST, 50)
     return Ks, ldk, Y, rho, X, WARM_TRAIN
+
+
+def warm_start_train(count: int = 65536, n: int = 1024, p: int = 4096, k: int = 50, *,
+                     seed: int = SEED_BASE + 6, sigma: float = 0.01):
+    """More training right-hand sides for the learned warm start, on the K of
+    warm_start_data (its first draw), from a separate stream: k positions drawn
+    with replacement per sample (a repeated position adds its N(0,1) values),
+    noise sigma, rho = ||x_true||_1.  Built sparsely, so 10^5 samples take
+    seconds.  Returns (Y float32 count x n, rho float64 count)."""
+    import scipy.sparse as sp
+    rng_k = np.random.Generator(np.random.PCG64(SEED_BASE + 5))
+    K64 = rng_k.standard_normal((n, p)) / np.sqrt(n)
+    Kw = bf16_bits_to_f64(_store(K64, DT_BF16, padded_ld(p, DT_BF16))[:, :p]).astype(np.float32)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Y = np.empty((count, n), np.float32)
+    rho = np.empty(count, np.float64)
+    chunk = 8192
+    for c0 in range(0, count, chunk):
+        m = min(chunk, count - c0)
+        idx = rng.integers(0, p, size=(m, k))
+        val = rng.standard_normal((m, k))
+        X = sp.csr_matrix((val.ravel(), idx.ravel(), np.arange(0, m * k + 1, k)), shape=(m, p))
+        X.sum_duplicates()
+        rho[c0:c0 + m] = np.asarray(abs(X).sum(axis=1)).ravel()
+        Y[c0:c0 + m] = (X.astype(np.float32) @ Kw.T) + sigma * rng.standard_normal((m, n)).astype(np.float32)
+    return Y, rho
