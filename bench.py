@@ -289,7 +289,7 @@ def run_batched(count, steps, dev, plain_sample=64):
 
 
 # ------------------------------------------------ shared-K form (c3b)
-def run_shared_k(nrhs, dev, verify=16, plain=8):
+def run_shared_k(nrhs, dev, verify=16, plain=8, pin=None):
     """Solves/s of nrhs right-hand sides on one K 2048 x 8192 BF16 (each from its own
     +-1 102-sparse signal), all in one gpl1_solve_shared_k call (tensor-core GEMMs),
     against the same instances solved one by one with gpl1_solve (plain form, a
@@ -307,6 +307,10 @@ def run_shared_k(nrhs, dev, verify=16, plain=8):
     K = torch.from_numpy(Ks.view(np.int16)).to(dev)
     Yd = torch.from_numpy(np.ascontiguousarray(Y)).to(dev)
     ctx = pkg.Context(dev.index or 0)
+    if pin:   # "cfg:1,cfg:splits": pinned choices for K^T R and K D instead of tuning
+        (c1, s1), (c2, s2) = [tuple(int(v) for v in t.split(":")) for t in pin.split(",")]
+        ctx.gemm_tuned_set((p, nrhs, 3 * n, n, 1), c1, s1)
+        ctx.gemm_tuned_set((n, nrhs, 3 * p, p, 8), c2, s2)
     prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=0.5 * TOL, max_iter=2000)
     ctx.solve_shared_k(K, Yd, rho, p=p, f_star=fstars, params=prm)          # warm-up
     torch.cuda.synchronize()
@@ -589,7 +593,7 @@ def run_ours(args, rank, world, local_rank):
     if args.batched_sample > 0:
         line["batched"] = run_batched(args.batched_sample, 3, dev)
     if args.shared_k > 0 and os.path.exists(os.path.join(ROOT, "tests", "golden", "c3b_fstar.json")):
-        line["shared_k"] = run_shared_k(args.shared_k, dev)
+        line["shared_k"] = run_shared_k(args.shared_k, dev, pin=args.shared_k_pin)
     if args.warm_start and os.path.exists(os.path.join(ROOT, "tests", "golden", "c4_fstar.json")):
         line["warm_start"] = run_warm_start(dev)
     print(json.dumps(line), flush=True)
@@ -620,6 +624,9 @@ def main():
                     help="also time this many ragged instances batched vs plain (0: skip)")
     ap.add_argument("--shared-k", type=int, default=1024,
                     help="also time this many right-hand sides on one shared K (0: skip)")
+    ap.add_argument("--shared-k-pin", default=None,
+                    help="pin the shared-K products' GEMM choices instead of tuning: 'cfg:1,cfg:splits' for "
+                         "K^T R and K D (to reproduce a configuration under a profiler)")
     ap.add_argument("--warm-start", type=int, default=1, help="also measure the learned warm start (0: skip)")
     ap.add_argument("--workload", choices=["c1", "c3a"], default="c1",
                     help="c3a: only the batched ragged form, all 512 instances")

@@ -234,6 +234,14 @@ gpl1_status gpl1_gemm_bf16_ex(gpl1_ctx* ctx, const void* A, long long M, long lo
 int gpl1_gemm_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* config, int* splits,
                     float* ms);
 
+/* Pins the choice for one product shape (shape[5] = {M, N, Kd, Ka, max_splits},
+ * as listed by gpl1_gemm_tuned) in the context's cache, so that the solve uses
+ * it without tuning: to reuse choices from an earlier run, or to reproduce a
+ * configuration under a profiler (which distorts the tuner's timings).  The
+ * tuned time of a pinned entry reads 0.  GPL1_ERR_INVALID_ARG for a config or
+ * split out of range. */
+gpl1_status gpl1_gemm_tuned_set(gpl1_ctx* ctx, const long long* shape, int config, int splits);
+
 /* Solve nrhs instances of eq. 2 that share one K (GPL1_BF16, n x p, row
  * stride ldk) and differ in y and rho, with Alg. GP + SS per instance: the
  * gradients 2 K^T r and the products K d of all instances are formed as

@@ -30,7 +30,7 @@ ALGORITHMIC = (0, 3, 4, 5, 6)
 
 EXPORTS = ["gpl1_create", "gpl1_destroy", "gpl1_set_stream", "gpl1_last_error", "gpl1_params_default",
            "gpl1_project", "gpl1_solve", "gpl1_solve_batched", "gpl1_solve_noalloc", "gpl1_gemm_bf16",
-           "gpl1_gemm_bf16_ex", "gpl1_gemm_tuned", "gpl1_solve_shared_k", "gpl1_lista_forward",
+           "gpl1_gemm_bf16_ex", "gpl1_gemm_tuned", "gpl1_gemm_tuned_set", "gpl1_solve_shared_k", "gpl1_lista_forward",
            "gpl1_lista_grad", "gpl1_lista_train", "gpl1_plan_create", "gpl1_plan_run", "gpl1_plan_destroy"]
 
 
@@ -105,6 +105,8 @@ def lib():
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_float)]
         L.gpl1_gemm_tuned.restype = ctypes.c_int
+        L.gpl1_gemm_tuned_set.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
+                                          ctypes.c_int]
         L.gpl1_solve_shared_k.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
                                           ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
@@ -248,6 +250,11 @@ class Context:
             L.gpl1_gemm_tuned(self._h, i, shp, ctypes.byref(cfg), ctypes.byref(spl), ctypes.byref(ms))
             out.append({"shape": tuple(shp), "config": cfg.value, "splits": spl.value, "ms": ms.value})
         return out
+
+    def gemm_tuned_set(self, shape, config, splits):
+        """gpl1_gemm_tuned_set: pin (config, splits) for shape (M, N, Kd, Ka, max_splits)."""
+        shp = (ctypes.c_longlong * 5)(*[int(v) for v in shape])
+        self._check(lib().gpl1_gemm_tuned_set(self._h, shp, int(config), int(splits)))
 
     # ------------------------------------------------ learned warm start
     @staticmethod

@@ -761,6 +761,16 @@ extern "C" gpl1_status gpl1_gemm_bf16_ex(gpl1_ctx* ctx, const void* A, long long
   return gemm_impl(ctx, A, M, Ka, lda, B, N, Kd, ldb, out, ldo, scale, config, splits, split_stride);
 }
 
+extern "C" gpl1_status gpl1_gemm_tuned_set(gpl1_ctx* ctx, const long long* shape, int config, int splits) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  if (!shape) return fail(ctx, GPL1_ERR_INVALID_ARG, "shape is NULL");
+  if (config < 0 || config >= kGemmConfigs) return fail(ctx, GPL1_ERR_INVALID_ARG, "config must lie in [0, %d)", kGemmConfigs);
+  if (shape[2] < 64 || shape[2] % 64 || shape[4] < 1 || splits < 1 || splits > shape[4] || splits > shape[2] / 64)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "need Kd a multiple of 64 and 1 <= splits <= min(max_splits, Kd / 64)");
+  ctx->gemm_tuned[std::vector<long long>(shape, shape + 5)] = GemmChoice{config, splits, 0.f};
+  return GPL1_OK;
+}
+
 extern "C" int gpl1_gemm_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* config, int* splits,
                                float* ms) {
   if (!ctx) return -1;

@@ -97,3 +97,28 @@ def test_shared_k_from_given_x0(gpu_ctx):
         assert res[b].status == 0, (b, res[b].as_dict())
         assert (oracle.objective(probs[b], Xh[b]) - fstar[b]) / fstar[b] <= 1e-6
         assert np.abs(Xh[b]).sum() <= rho[b] * (1 + 1e-6)
+
+
+def test_shared_k_with_pinned_gemm_choices(gpu_ctx):
+    """gpl1_gemm_tuned_set: a pinned configuration and split (here BN 256 with the
+    second product split in 3) is used as given (tuned time 0) and solves as well."""
+    n, p, nrhs, k = 256, 1024, 8, 12
+    Ks, ldk, Y, rho, probs = instances(n, p, nrhs, k, seed=29)
+    fstar = np.array([oracle.reference_solve(pr)[1].f for pr in probs])
+    ctx = pkg.Context(0)
+    ctx.gemm_tuned_set((p, nrhs, 3 * n, n, 1), 1, 1)
+    ctx.gemm_tuned_set((n, nrhs, 3 * p, p, 8), 1, 3)
+    with pytest.raises(pkg.Gpl1Error):
+        ctx.gemm_tuned_set((n, nrhs, 3 * p, p, 8), 4, 1)
+    K = torch.from_numpy(Ks.view(np.int16)).to(DEV)
+    Yd = torch.from_numpy(Y).to(DEV)
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, max_iter=3000)
+    X, res = ctx.solve_shared_k(K, Yd, rho, p=p, f_star=fstar, params=prm)
+    torch.cuda.synchronize()
+    tuned = {t["shape"]: t for t in ctx.gemm_tuned()}
+    assert tuned[(n, nrhs, 3 * p, p, 8)]["splits"] == 3 and tuned[(n, nrhs, 3 * p, p, 8)]["ms"] == 0.0
+    Xh = X.double().cpu().numpy()
+    for b in range(nrhs):
+        assert res[b].status == 0
+        assert (oracle.objective(probs[b], Xh[b]) - fstar[b]) / fstar[b] <= 1e-6
+    ctx.close()
