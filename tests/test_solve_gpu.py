@@ -189,3 +189,20 @@ def test_bounded_wait_reports_timeout(gpu_ctx):
     assert res.status == 6 and res.stop == 4
     x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=1e-6, f_star=GOLDEN["c0"]["f_star"])
     assert res.status == 0 and rel_gap(prob, x, GOLDEN["c0"]["f_star"]) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype,p", [(W.DT_F32, 16800), (W.DT_F64, 3840), (W.DT_BF16, 16800)])
+def test_largest_p_the_kernel_stages(gpu_ctx, dtype, p):
+    """p at the limit of the staged x/v vector in shared memory (35 x 480 float
+    entries, 8 x 480 double entries), with a ragged last box of columns."""
+    prob = small(192, p, 12, dtype, seed=p + dtype, rho_scale=0.8)
+    xs, rs, _ = oracle.reference_solve(prob)
+    x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000)
+    assert res.status == 0, res.as_dict()
+    assert rel_gap(prob, x, rs.f) <= 1e-6
+    assert np.abs(x).sum() <= prob.rho * (1 + 1e-6)
+    # one column more than the staging holds is refused, not run
+    K, y = to_dev(small(8, p + 1, 1, dtype, seed=1))
+    with pytest.raises(pkg.Gpl1Error) as e:
+        gpu_ctx.solve(K, y, 1.0)
+    assert e.value.status == 7
