@@ -846,7 +846,7 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
   }
   // workspace
   const size_t N = static_cast<size_t>(nrhs), nn = static_cast<size_t>(n), pp = static_cast<size_t>(p);
-  size_t off = 256;   // [0] done count, [64] gemm error flag
+  size_t off = 256;   // [0] done count, [64] gemm error flag, [128] restart counts
   auto take = [&](size_t bytes) {
     const size_t o = off;
     off = align_up(off + bytes, 256);
@@ -857,6 +857,7 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
   const size_t o_st = take(N * mr_state_bytes()), o_res = take(N * sizeof(gpl1_result));
   const size_t o_rho = take(N * 8), o_fs = take(N * 8);
   const size_t o_xp = take(mr_exact_part_bytes(static_cast<int>(n), static_cast<int>(p), nrhs));
+  const size_t o_rl = take(2 * N * sizeof(int));
   st = ensure_ws(ctx, off);
   if (st) return st;
   uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
@@ -873,6 +874,8 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
   double* rho_d = reinterpret_cast<double*>(ws + o_rho);
   double* fs_d = reinterpret_cast<double*>(ws + o_fs);
   void* xpart = ws + o_xp;   // column partials of the exact K x
+  int* restart_cnt = reinterpret_cast<int*>(ws + 128);   // [2], zeroed with the counters
+  int* restart_list = reinterpret_cast<int*>(ws + o_rl);
   cudaStream_t s = ctx->stream;
   GPL1_CUDA(cudaMemsetAsync(ws, 0, 256, s), "cudaMemsetAsync");
   GPL1_CUDA(cudaMemsetAsync(G[1], 0, N * pp * 4, s), "cudaMemsetAsync");
@@ -911,12 +914,15 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
     int e = launch_gemm_bf16_cfg(ctx->encode, Kt, static_cast<int>(p), static_cast<int>(n), n, Rs, nrhs,
                                  static_cast<int>(3 * n), 3 * n, Gc, p, 2.f, gerr, tmo, c1.cfg, 1, 0, s);
     if (e) return e == -1 ? fail(ctx, GPL1_ERR_CUDA, "tensor map") : cuda_fail(ctx, static_cast<cudaError_t>(e), "gemm 1");
-    GPL1_CUDA(launch_mr_phase_p(Gc, Gp, X, ldx, D, DXs, static_cast<int>(p), nrhs, k, states, sp, s), "phase P");
+    GPL1_CUDA(launch_mr_phase_p(Gc, Gp, X, ldx, D, DXs, static_cast<int>(p), nrhs, k, states, sp, restart_cnt,
+                                restart_list, s),
+              "phase P");
     e = launch_gemm_bf16_cfg(ctx->encode, K, static_cast<int>(n), static_cast<int>(p), ldk, DXs, nrhs,
                              static_cast<int>(3 * p), 3 * p, KD, n, 1.f, gerr, tmo, c2.cfg, c2.splits,
                              static_cast<long long>(N * nn), s);
     if (e) return e == -1 ? fail(ctx, GPL1_ERR_CUDA, "tensor map") : cuda_fail(ctx, static_cast<cudaError_t>(e), "gemm 2");
-    GPL1_CUDA(launch_mr_exact_kx(Kt, X, ldx, xpart, static_cast<int>(n), static_cast<int>(p), nrhs, states, s),
+    GPL1_CUDA(launch_mr_exact_kx(Kt, X, ldx, xpart, static_cast<int>(n), static_cast<int>(p), nrhs, states,
+                                 restart_cnt, restart_list, k, ctx->num_sms, s),
               "exact K x");
     GPL1_CUDA(launch_mr_phase_l(KD, c2.splits, static_cast<long long>(N * nn), xpart, Y, ldy, X, ldx, D, Rs,
                                 static_cast<int>(n), static_cast<int>(p), nrhs, k, states, sp, rdev, done_count, s),

@@ -62,14 +62,16 @@ cudaError_t launch_mr_init(const float* Y, long long ldy, float* X, long long ld
                            cudaStream_t s);
 cudaError_t launch_mr_phase_p(const float* G, const float* Gprev, const float* X, long long ldx, float* D,
                               uint16_t* DXs, int p, int nrhs, int k, void* states, const SolveParams& prm,
-                              cudaStream_t s);
+                              int* restart_cnt, int* restart_list, cudaStream_t s);
 cudaError_t launch_mr_phase_l(float* KD, int splits, long long split_stride, const void* xpart, const float* Y,
                               long long ldy, float* X, long long ldx, const float* D, uint16_t* Rs, int n, int p,
                               int nrhs, int k, void* states, const SolveParams& prm, gpl1_result* res,
                               int* done_count, cudaStream_t s);
 size_t mr_exact_part_bytes(int n, int p, int nrhs);
+// restart_cnt: 2 ints (zero at the start of a solve); restart_list: 2 x nrhs ints.
 cudaError_t launch_mr_exact_kx(const void* Kt, const float* X, long long ldx, void* xpart, int n, int p, int nrhs,
-                               const void* states, cudaStream_t s);
+                               const void* states, const int* restart_cnt, const int* restart_list, int k, int num_sms,
+                               cudaStream_t s);
 cudaError_t launch_transpose_bf16(const void* K, long long ldk, void* Kt, int n, int p, cudaStream_t s);
 cudaError_t launch_mr_setup_x0(float* X, long long ldx, uint16_t* DXs, int p, int nrhs, const double* rho,
                                cudaStream_t s);

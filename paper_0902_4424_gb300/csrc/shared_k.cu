@@ -253,11 +253,31 @@ __device__ __forceinline__ float mr_dir(float x, float g, float ah, float th, fl
   return -(q.hi + (q.lo + (e + tl * s)));
 }
 
+// Restarts of r from the exact K x (see the file comment): on the first
+// iteration near the stop, on the iteration after a relative-gap stop was met
+// on a carried r, and every 8th iteration in between.  (Every 32nd saves
+// restarts but lets the drift into the line search: c4 then took 51.5
+// iterations on average instead of 47.2.)
+constexpr int kMrExactEvery = 8;   // near the stop, r restarts from the exact K x every 8 iterations
+
+__device__ __forceinline__ bool mr_restarts(const MrState& S) {
+  return !S.done && S.acc && S.acc_age % kMrExactEvery == 0;
+}
+
+// The instances that restart in iteration k are listed by phase P of k in
+// list[k & 1] (count cnt[k & 1]) for mr_exact_kx; phase P of k clears the
+// other count, which mr_exact_kx of k - 1 has consumed.
+struct MrRestartList {
+  int* cnt;    // [2]
+  int* list;   // [2][nrhs]
+};
+
 __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const float* Gprev, const float* X,
                                                          long long ldx, float* D, uint16_t* DXs, int p, int nrhs,
-                                                         int k, MrState* st, SolveParams prm) {
+                                                         int k, MrState* st, SolveParams prm, MrRestartList rl) {
   const int b = blockIdx.x, tid = threadIdx.x;
   MrState& S = st[b];
+  if (b == 0 && tid == 0) rl.cnt[(k + 1) & 1] = 0;
   if (S.done) return;   // the same value in every thread of the CTA
   extern __shared__ uint8_t mr_raw[];
   MrSmem& sm = *reinterpret_cast<MrSmem*>(mr_raw);
@@ -452,10 +472,10 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
     S.th = th;
     S.tl = tl;
     S.inside = tv.inside;
+    if (mr_restarts(S)) rl.list[(k & 1) * nrhs + atomicAdd(&rl.cnt[k & 1], 1)] = b;
   }
 }
 
-constexpr int kMrExactEvery = 8;   // near the stop, r restarts from the exact K x every 8 iterations
 constexpr int kMrRowsPerThread = 9; // n <= 9 * 480 rows for the accurate K x
 
 // Exact K x for the instances that restart r this iteration, split over
@@ -473,20 +493,12 @@ constexpr int kMrExactGroups = 3;    // 8-row groups per thread: n <= 3 * 256 * 
 
 int mr_exact_splits(int p) { return (p + kMrExactCols - 1) / kMrExactCols; }
 
-__device__ __forceinline__ bool mr_restarts(const MrState& S) {
-  return !S.done && S.acc && S.acc_age % kMrExactEvery == 0;
-}
 
-__global__ void __launch_bounds__(kMrExactThreads) mr_exact_kx(const uint16_t* __restrict__ Kt,
-                                                              const float* __restrict__ X, long long ldx,
-                                                              F2* __restrict__ part, int n, int p,
-                                                              const MrState* __restrict__ st) {
-  const int b = blockIdx.x, s = blockIdx.y, S = gridDim.y, tid = threadIdx.x;
-  const MrState& M = st[b];
-  if (!mr_restarts(M)) return;   // the same value in every thread
-  __shared__ int sup_j[kMrExactCols];
-  __shared__ float sup_x[kMrExactCols];
-  __shared__ int sup_n;
+// One (instance b, column range s) item of mr_exact_kx.
+__device__ __forceinline__ void mr_exact_item(const uint16_t* __restrict__ Kt, const float* __restrict__ X,
+                                              long long ldx, F2* __restrict__ part, int n, int p, int S,
+                                              const MrState& M, int b, int s, int tid, int* sup_j, float* sup_x,
+                                              int& sup_n) {
   const int j0 = static_cast<int>(static_cast<long long>(s) * p / S);
   const int j1 = static_cast<int>(static_cast<long long>(s + 1) * p / S);
   const float xsc = M.xscale;
@@ -540,6 +552,22 @@ __global__ void __launch_bounds__(kMrExactThreads) mr_exact_kx(const uint16_t* _
     if (i0 >= n) break;
 #pragma unroll
     for (int r = 0; r < 8; ++r) out[i0 + r] = two_sum(acc[m][r].hi, acc[m][r].lo);
+  }
+}
+
+__global__ void __launch_bounds__(kMrExactThreads) mr_exact_kx(const uint16_t* __restrict__ Kt,
+                                                              const float* __restrict__ X, long long ldx,
+                                                              F2* __restrict__ part, int n, int p, int S,
+                                                              const MrState* __restrict__ st, const int* cnt,
+                                                              const int* list) {
+  __shared__ int sup_j[kMrExactCols];
+  __shared__ float sup_x[kMrExactCols];
+  __shared__ int sup_n;
+  const int items = *cnt * S, tid = threadIdx.x;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {   // (listed instance, column range)
+    const int b = list[item / S], s = item % S;
+    mr_exact_item(Kt, X, ldx, part, n, p, S, st[b], b, s, tid, sup_j, sup_x, sup_n);
+    __syncthreads();   // the lists in shared memory are reused by the next item
   }
 }
 
@@ -794,7 +822,7 @@ cudaError_t launch_mr_init(const float* Y, long long ldy, float* X, long long ld
 }
 cudaError_t launch_mr_phase_p(const float* G, const float* Gprev, const float* X, long long ldx, float* D,
                               uint16_t* DXs, int p, int nrhs, int k, void* states, const SolveParams& prm,
-                              cudaStream_t s) {
+                              int* restart_cnt, int* restart_list, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(mr_phase_p, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -803,7 +831,8 @@ cudaError_t launch_mr_phase_p(const float* G, const float* Gprev, const float* X
     attr = true;
   }
   mr_phase_p<<<nrhs, kConsumers, mr_smem_bytes(p, 2), s>>>(G, Gprev, X, ldx, D, DXs, p, nrhs, k,
-                                                      static_cast<MrState*>(states), prm);
+                                                          static_cast<MrState*>(states), prm,
+                                                          MrRestartList{restart_cnt, restart_list});
   return cudaGetLastError();
 }
 cudaError_t launch_mr_phase_l(float* KD, int splits, long long split_stride, const void* xpart, const float* Y,
@@ -819,10 +848,13 @@ size_t mr_exact_part_bytes(int n, int p, int nrhs) {
   return static_cast<size_t>(nrhs) * mr_exact_splits(p) * n * sizeof(F2);
 }
 cudaError_t launch_mr_exact_kx(const void* Kt, const float* X, long long ldx, void* xpart, int n, int p, int nrhs,
-                               const void* states, cudaStream_t s) {
-  const dim3 grid(nrhs, mr_exact_splits(p));
+                               const void* states, const int* restart_cnt, const int* restart_list, int k, int num_sms,
+                               cudaStream_t s) {
+  // persistent over the (listed instance, column range) items of this iteration
+  const int grid = std::min(3 * num_sms, nrhs * mr_exact_splits(p));
   mr_exact_kx<<<grid, kMrExactThreads, 0, s>>>(static_cast<const uint16_t*>(Kt), X, ldx, static_cast<F2*>(xpart), n,
-                                               p, static_cast<const MrState*>(states));
+                                               p, mr_exact_splits(p), static_cast<const MrState*>(states),
+                                               restart_cnt + (k & 1), restart_list + (k & 1) * nrhs);
   return cudaGetLastError();
 }
 cudaError_t launch_transpose_bf16(const void* K, long long ldk, void* Kt, int n, int p, cudaStream_t s) {
