@@ -458,6 +458,72 @@ def run_warm_start(dev, steps=3000, batch=256, ntrain=65536, lr=3e-4):
             "note": "warm time includes the network's inference; both solved in one shared-K call"}
 
 
+# ------------------------------------------------ radius sweep (c5)
+def run_rho_sweep(dev):
+    """The paper's Gaussian shape (K 1848 x 8192, ||K|| = 1, 2% noise; rows padded to
+    1856) solved for 50 radii from 0.05 to 1.2 ||x_true||_1 (workloads.rho_sweep):
+    (a) all radii in one gpl1_solve_shared_k call, (b) one gpl1_solve per radius in
+    increasing order, each started from the previous solution (continuation along
+    rho), (c) one cold gpl1_solve per radius.  Each stops at relative gap 5e-7
+    against the oracle's optimum of that radius (tests/golden/c5_fstar.json), the
+    gap taken relative to max(f*, 1e-6 ||y||^2) (f* is tiny once rho allows a
+    near-exact fit); every returned x is checked in FP64."""
+    import torch
+
+    import paper_0902_4424_gb300 as pkg
+    import workloads as W
+    with open(os.path.join(ROOT, "tests", "golden", "c5_fstar.json")) as fh:
+        fstars = json.load(fh)["f_star"]
+    Ks, ldk, n, y, rho, xt = W.rho_sweep()
+    p, R = xt.shape[0], len(rho)
+    K = torch.from_numpy(Ks.view(np.int16)).to(dev)
+    yd = torch.from_numpy(y).to(dev)
+    Yd = yd.unsqueeze(0).repeat(R, 1).contiguous()
+    ctx = pkg.Context(dev.index or 0)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=0.5 * TOL, max_iter=20000)
+    y2 = float(np.dot(y.astype(np.float64), y.astype(np.float64)))
+    den = [max(f, 1e-6 * y2) for f in fstars]
+    prob = W.Problem(Ks, n, p, ldk, W.DT_BF16, y.astype(np.float32), 0.0, xt, "c5")
+
+    def gaps(X):
+        return [(objective_f64(prob, X[b]) - fstars[b]) / den[b] for b in range(R)]
+    ctx.solve_shared_k(K, Yd, rho, p=p, f_star=fstars, params=prm)   # warm-up and tuning
+    a, b = ev(), ev()
+    a.record(stream)
+    Xs, rs = ctx.solve_shared_k(K, Yd, rho, p=p, f_star=fstars, params=prm)
+    b.record(stream)
+    b.synchronize()
+    shared_ms = a.elapsed_time(b)
+    g_shared = gaps(Xs.double().cpu().numpy())
+    out = {"workload": f"c5_rhosweep1848x8192_bf16_{R}", "radii": R,
+           "shared_k": {"solves_per_s": R / (shared_ms / 1e3), "ms": shared_ms,
+                        "iters_mean": statistics.mean(r.iters for r in rs), "ok": sum(r.status == 0 for r in rs),
+                        "verified_max_rel_gap": max(g_shared)}}
+    for mode in ("continuation", "cold"):
+        x = torch.zeros(p, dtype=torch.float32, device=dev)
+        xs, its, oks = [], [], 0
+        a, b = ev(), ev()
+        a.record(stream)
+        for q in range(R):
+            if mode == "cold":
+                x = torch.zeros(p, dtype=torch.float32, device=dev)
+            x, r = ctx.solve(K, yd, float(rho[q]), x=x, p=p, params=prm, f_star=fstars[q])
+            xs.append(x.clone())
+            its.append(r.iters)
+            oks += r.status == 0
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        g = gaps(torch.stack(xs).double().cpu().numpy())
+        out[mode] = {"solves_per_s": R / (ms / 1e3), "ms": ms, "iters_mean": statistics.mean(its), "ok": oks,
+                     "verified_max_rel_gap": max(g)}
+    out["stop"] = f"kernel stop gap<={0.5 * TOL:g} vs oracle f* per radius, relative to max(f*, 1e-6 ||y||^2)"
+    ctx.close()
+    return out
+
+
 # -------------------------------------------------------------- GPU path
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -596,6 +662,8 @@ def run_ours(args, rank, world, local_rank):
         line["shared_k"] = run_shared_k(args.shared_k, dev, pin=args.shared_k_pin)
     if args.warm_start and os.path.exists(os.path.join(ROOT, "tests", "golden", "c4_fstar.json")):
         line["warm_start"] = run_warm_start(dev)
+    if args.rho_sweep and os.path.exists(os.path.join(ROOT, "tests", "golden", "c5_fstar.json")):
+        line["rho_sweep"] = run_rho_sweep(dev)
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -628,6 +696,7 @@ def main():
                     help="pin the shared-K products' GEMM choices instead of tuning: 'cfg:1,cfg:splits' for "
                          "K^T R and K D (to reproduce a configuration under a profiler)")
     ap.add_argument("--warm-start", type=int, default=1, help="also measure the learned warm start (0: skip)")
+    ap.add_argument("--rho-sweep", type=int, default=1, help="also measure the 50-radius sweep (0: skip)")
     ap.add_argument("--workload", choices=["c1", "c3a"], default="c1",
                     help="c3a: only the batched ragged form, all 512 instances")
     args = ap.parse_args()

@@ -8,6 +8,7 @@ no decrease of f for 30 iterations).  Nothing here touches the CUDA path.
     python tests/golden/make_golden.py c3a      # the ragged batch: c3a_fstar.json
     python tests/golden/make_golden.py c3b      # the shared-K right-hand sides: c3b_fstar.json
     python tests/golden/make_golden.py c4       # the warm-start test samples: c4_fstar.json
+    python tests/golden/make_golden.py c5       # the radius sweep: c5_fstar.json
 """
 import json
 import os
@@ -60,6 +61,23 @@ def main_c3a(count=512):
                    "solver": "oracle.floor_solve"}, fh, indent=0)
 
 
+def main_c5():
+    """tests/golden/c5_fstar.json: f* of each radius of the sweep (workloads.rho_sweep),
+    by the oracle's floor solve."""
+    out = os.path.join(os.path.dirname(OUT), "c5_fstar.json")
+    t = time.time()
+    Ks, ldk, n, y, rho, x = W.rho_sweep()
+    p = x.shape[0]
+    fs = []
+    for b, r in enumerate(rho):
+        prob = W.Problem(Ks, n, p, ldk, W.DT_BF16, y.copy(), float(r), x, f"c5_{b}")
+        fs.append(oracle.floor_solve(prob)[1].f)
+        print(b, r, fs[-1], f"{time.time() - t:.0f}s", flush=True)
+    with open(out, "w") as fh:
+        json.dump({"workload": "c5_rhosweep1848x8192_bf16_50", "rho": [float(r) for r in rho], "f_star": fs,
+                   "solver": "oracle.floor_solve"}, fh, indent=0)
+
+
 def main_c3b(nrhs=1024):
     """tests/golden/c3b_fstar.json: f* of each right-hand side of the shared-K
     workload (K 2048 x 8192 BF16), by the oracle's floor solve."""
@@ -99,6 +117,9 @@ if __name__ == "__main__":
     args = sys.argv[1:]
     if args == ["c4"]:
         main_c4()
+        sys.exit(0)
+    if args == ["c5"]:
+        main_c5()
         sys.exit(0)
     if args == ["c3a"]:
         main_c3a()

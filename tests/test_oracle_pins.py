@@ -324,6 +324,26 @@ def test_golden_c3a_fstar_match_oracle():
         assert abs(f - gold["f_star"][i]) <= 1e-12 * gold["f_star"][i]
 
 
+def test_golden_c5_fstar_match_oracle_and_the_path():
+    """The stored optima of the radius sweep are the oracle's (recompute the smallest
+    radius), and they trace the solution path: f* falls as rho grows (a larger
+    ball), convex in rho (the value function of a convex problem in its radius),
+    and at rho = ||x_true||_1 it sits near the noise level."""
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c5_fstar.json")))
+    Ks, ldk, n, y, rho, xt = W.rho_sweep()
+    assert np.allclose(gold["rho"], rho, rtol=1e-15)
+    prob = W.Problem(Ks, n, xt.shape[0], ldk, W.DT_BF16, y.copy(), float(rho[0]), xt, "c5_0")
+    f0 = oracle.floor_solve(prob)[1].f
+    assert abs(f0 - gold["f_star"][0]) <= 1e-12 * f0
+    f = np.array(gold["f_star"])
+    assert np.all(np.diff(f) < 0)
+    slope = np.diff(f) / np.diff(rho)
+    assert np.all(np.diff(slope) >= -1e-9 * np.abs(slope[:-1]))
+    K = W.bf16_bits_to_f64(Ks[:, :xt.shape[0]])
+    noise2 = float(np.sum((y.astype(np.float64) - K @ xt) ** 2))
+    assert 0.2 * noise2 <= f[-1] <= noise2
+
+
 # ------------------------------------------------------- learned warm start
 from oracle import lista  # noqa: E402
 
@@ -389,3 +409,18 @@ def test_lista_backward_matches_finite_differences():
         fp = lista.loss(lista.forward(K, W, tp, Y)[0][-1], Xt)
         fm = lista.loss(lista.forward(K, W, tm, Y)[0][-1], Xt)
         assert abs((fp - fm) / (2 * h) - dth[l]) <= 1e-6 * max(1.0, abs(dth[l]))
+
+
+def test_nonmonotone_line_search_invariant():
+    """M > 1 (the nonmonotone Armijo rule of Alg. GP, Step 4): every accepted value
+    lies below the largest of the last M (gT d < 0), f need not decrease at every
+    step, and the run reaches the same optimum as the monotone reference."""
+    prob = W.config0()
+    _, ref, _ = oracle.reference_solve(prob)
+    M = 10
+    x, r, tr = oracle.gpss(prob, trace=True, f_star=ref.f, tol=1e-6, M=M)
+    assert r.stop == 0 and (r.f - ref.f) <= 1e-6 * ref.f
+    f = tr[:, 0]
+    for k in range(1, len(f)):
+        assert f[k] < max(f[max(0, k - M):k]) or f[k] == f[k - 1] == 0.0
+    assert np.abs(x).sum() <= prob.rho * (1 + 1e-12)

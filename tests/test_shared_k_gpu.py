@@ -145,3 +145,33 @@ def test_shared_k_full_size_against_stored_optima(gpu_ctx):
         pr = W.Problem(Ks, n, p, ldk, W.DT_BF16, Y[q].copy(), float(rho[q]), Xt[q], f"c3b_{q}")
         assert (oracle.objective(pr, Xh[q]) - fstars[q]) / fstars[q] <= 1e-6, q
         assert np.abs(Xh[q]).sum() <= rho[q] * (1 + 1e-6)
+
+
+def test_radius_sweep_shared_and_continuation():
+    """The radius sweep (K 1848 x 8192 with ||K|| = 1, 2% noise, 50 radii): all radii
+    in one shared-K call, and a continuation along rho (each gpl1_solve started from
+    the previous radius' solution), every x within the gap of its stored optimum."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c5_fstar.json")))
+    fstars = gold["f_star"]
+    Ks, ldk, n, y, rho, xt = W.rho_sweep()
+    p, R = xt.shape[0], len(rho)
+    prob = W.Problem(Ks, n, p, ldk, W.DT_BF16, y.copy(), 0.0, xt, "c5")
+    ctx = pkg.Context(0)
+    K = torch.from_numpy(Ks.view(np.int16)).to(DEV)
+    yd = torch.from_numpy(y).to(DEV)
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, max_iter=20000)
+    X, res = ctx.solve_shared_k(K, yd.unsqueeze(0).repeat(R, 1).contiguous(), rho, p=p, f_star=fstars, params=prm)
+    torch.cuda.synchronize()
+    Xh = X.double().cpu().numpy()
+    for b in range(R):
+        assert res[b].status == 0, (b, res[b].as_dict())
+        assert (oracle.objective(prob, Xh[b]) - fstars[b]) / fstars[b] <= 1e-6, b
+    x = torch.zeros(p, dtype=torch.float32, device=DEV)
+    for q in range(0, R, 7):
+        x, r = ctx.solve(K, yd, float(rho[q]), x=x, p=p, params=prm, f_star=fstars[q])
+        torch.cuda.synchronize()
+        assert r.status == 0
+        assert (oracle.objective(prob, x.double().cpu().numpy()) - fstars[q]) / fstars[q] <= 1e-6, q
+    ctx.close()

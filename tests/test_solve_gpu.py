@@ -206,3 +206,19 @@ def test_largest_p_the_kernel_stages(gpu_ctx, dtype, p):
     with pytest.raises(pkg.Gpl1Error) as e:
         gpu_ctx.solve(K, y, 1.0)
     assert e.value.status == 7
+
+
+def test_nonmonotone_line_search_matches_oracle(gpu_ctx):
+    """M = 10: the FP64 path takes the oracle's steps through the early iterations,
+    and the FP32 path reaches the 1e-6 gap."""
+    prob = W.config0()
+    for iters in (3, 12):
+        x, res = gpu_solve(gpu_ctx, prob, stop_rule=0, max_iter=iters, M=10)
+        xo, ro, tr = oracle.gpss(prob, trace=True, tol=0.0, max_iter=iters, M=10)
+        assert res.iters == iters
+        np.testing.assert_allclose(x, xo, rtol=0, atol=1e-10 * np.abs(xo).max())
+    prob = small(300, 1000, 15, W.DT_F32, seed=91)
+    xs, rs, _ = oracle.reference_solve(prob)
+    x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000, M=10)
+    assert res.status == 0, res.as_dict()
+    assert rel_gap(prob, x, rs.f) <= 1e-6

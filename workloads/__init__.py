@@ -236,3 +236,34 @@ def warm_start_train(count: int = 65536, n: int = 1024, p: int = 4096, k: int = 
         rho[c0:c0 + m] = np.asarray(abs(X).sum(axis=1)).ravel()
         Y[c0:c0 + m] = (X.astype(np.float32) @ Kw.T) + sigma * rng.standard_normal((m, n)).astype(np.float32)
     return Y, rho
+
+
+def rho_sweep(n: int = 1848, p: int = 8192, k: int = 120, count: int = 50, *, seed: int = SEED_BASE + 7,
+              noise: float = 0.02, lo: float = 0.05, hi: float = 1.0):
+    """The paper's Gaussian test shape (Sec. 4) as a sweep over the radius: K
+    n x p N(0,1) scaled to ||K||_2 = 1 (power iteration on the float64 draw),
+    stored BF16 with its rows padded with zeros to a multiple of 64 (zero rows
+    leave eq. 2 unchanged); x_true k-sparse N(0,1); y = K x_true + e with
+    ||e|| = noise ||K x_true||; `count` radii geometric from lo to hi times
+    ||x_true||_1.  Returns (K stored n_pad x ldk, ldk, n_pad, y float32 n_pad,
+    rho float64 count, x_true)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    G = rng.standard_normal((n, p))
+    v = rng.standard_normal(p)
+    for _ in range(60):   # power iteration for ||G||_2
+        w = G.T @ (G @ v)
+        v = w / np.linalg.norm(w)
+    K64 = G / np.sqrt(np.linalg.norm(G.T @ (G @ v)))
+    n_pad = ((n + 63) // 64) * 64
+    Kp = np.zeros((n_pad, p))
+    Kp[:n] = K64
+    ldk = padded_ld(p, DT_BF16)
+    Ks = _store(Kp, DT_BF16, ldk)
+    Kw = bf16_bits_to_f64(Ks[:, :p])
+    x_true = _sparse_signal(rng, p, k, "gauss")
+    clean = Kw @ x_true
+    e = rng.standard_normal(n_pad)
+    e[n:] = 0.0
+    y = (clean + noise * np.linalg.norm(clean) / np.linalg.norm(e) * e).astype(np.float32)
+    rho = np.abs(x_true).sum() * np.geomspace(lo, hi, count)
+    return Ks, ldk, n_pad, y, rho, x_true
