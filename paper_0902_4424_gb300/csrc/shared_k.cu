@@ -289,8 +289,11 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
   const float* g = G + static_cast<long long>(b) * p;
   const float* gp = Gprev + static_cast<long long>(b) * p;
   const float* x = X + b * ldx;
-  // z^T z, g^T x, max |g|, ||x||_1
-  F2 zz{0.f, 0.f}, gx{0.f, 0.f}, l1{0.f, 0.f};
+  // z^T z, g^T x, max |g|, ||x||_1.  z^T z (for a steplength) takes plain FP32
+  // sums; g^T x (the Frank-Wolfe certificate, a difference of large terms near
+  // the stop) and ||x||_1 (the feasibility check) float pairs.
+  F2 gx{0.f, 0.f}, l1{0.f, 0.f};
+  float zzf = 0.f;
   float pm = 0.f;
   constexpr int CH = 6;   // the loads of a chunk are issued together
   for (int e0 = 0; e0 < neu; e0 += CH) {
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
       if (e0 + c >= neu) break;
       if (k > 0) {
         const float z = gv[c] - gq[c];
-        zz = f2_fma(zz, z, z);
+        zzf = fmaf(z, z, zzf);
       }
       gx = f2_fma(gx, gv[c], xv[c]);
       l1 = f2_add(l1, fabsf(xv[c]));
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
       gs[o] = gv[c];
     }
   }
-  F2 red[3] = {zz, gx, l1};
+  F2 red[3] = {F2{zzf, 0.f}, gx, l1};
   unsigned mx = __float_as_uint(pm);
   lead_reduce<3>(red, mx, sm.sc);
   if (tid == 0) {
@@ -436,7 +439,8 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
   // direction, its sums, and the BF16 terms of d for K D^T
   float* d = D + static_cast<long long>(b) * p;
   uint16_t* dd_s = DXs + static_cast<long long>(b) * 3 * p;
-  F2 sgd{0.f, 0.f}, sdd{0.f, 0.f};
+  F2 sgd{0.f, 0.f};   // its sign decides the line search near the stop: float pairs
+  float sddf = 0.f;
   unsigned nz = 0;
   for (int e0 = 0; e0 < neu; e0 += CH) {
     float xr[CH];   // x from memory: a chunk's loads are issued before its stores
@@ -453,7 +457,7 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
       const float dj = mr_dir(xj, gj, ah, th, tl, tv.inside);
       d[j] = dj;
       sgd = f2_fma(sgd, gj, dj);
-      sdd = f2_fma(sdd, dj, dj);
+      sddf = fmaf(dj, dj, sddf);
       nz |= dj != 0.f ? 1u : 0u;
       uint16_t h, m, l;
       split3(dj, h, m, l);
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
       dd_s[2 * p + j] = l;
     }
   }
-  F2 v2[2] = {sgd, sdd};
+  F2 v2[2] = {sgd, F2{sddf, 0.f}};
   unsigned nzm = nz;
   lead_reduce<2>(v2, nzm, sm.sc);
   if (tid == 0) {
