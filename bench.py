@@ -519,6 +519,20 @@ def run_rho_sweep(dev):
         g = gaps(torch.stack(xs).double().cpu().numpy())
         out[mode] = {"solves_per_s": R / (ms / 1e3), "ms": ms, "iters_mean": statistics.mean(its), "ok": oks,
                      "verified_max_rel_gap": max(g)}
+    # isochrones: all radii under a fixed iteration budget (no stop rule), the time of
+    # the call and the gap each radius reached
+    iso = []
+    for budget in (4, 8, 16, 32):
+        prm_b = pkg.params_default(stop_rule=0, max_iter=budget)
+        a, b = ev(), ev()
+        a.record(stream)
+        Xb, _ = ctx.solve_shared_k(K, Yd, rho, p=p, params=prm_b)
+        b.record(stream)
+        b.synchronize()
+        g = gaps(Xb.double().cpu().numpy())
+        iso.append({"iterations": budget, "ms": a.elapsed_time(b), "gap_median": float(np.median(g)),
+                    "gap_max": float(max(g))})
+    out["isochrones"] = iso
     out["stop"] = f"kernel stop gap<={0.5 * TOL:g} vs oracle f* per radius, relative to max(f*, 1e-6 ||y||^2)"
     ctx.close()
     return out

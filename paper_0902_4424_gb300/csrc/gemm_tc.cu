@@ -109,6 +109,8 @@ __global__ void __launch_bounds__(128, 1) gemm_bf16_tn(const __grid_constant__ C
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
+  pdl_wait();   // the operands come from the previous kernel of the stream
+  pdl_trigger();
 
   if (warp == 0 && lane == 0) {   // TMA producer
     int kb = 0;
@@ -211,8 +213,7 @@ cudaError_t launch_cfg(const CUtensorMap& ta, const CUtensorMap& tb, const GemmA
     set_for = dev;
   }
   const dim3 grid((g.M + kTcBM - 1) / kTcBM, (g.N + BN - 1) / BN, g.splits);
-  gemm_bf16_tn<BN, ST><<<grid, 128, smem, stream>>>(ta, tb, g);
-  return cudaGetLastError();
+  return launch_pdl(gemm_bf16_tn<BN, ST>, grid, dim3(128), smem, stream, ta, tb, g);
 }
 
 }  // namespace

@@ -276,6 +276,8 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_p(const float* G, const f
                                                          long long ldx, float* D, uint16_t* DXs, int p, int nrhs,
                                                          int k, MrState* st, SolveParams prm, MrRestartList rl) {
   const int b = blockIdx.x, tid = threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
   MrState& S = st[b];
   if (b == 0 && tid == 0) rl.cnt[(k + 1) & 1] = 0;
   if (S.done) return;   // the same value in every thread of the CTA
@@ -567,6 +569,8 @@ __global__ void __launch_bounds__(kMrExactThreads) mr_exact_kx(const uint16_t* _
   __shared__ int sup_j[kMrExactCols];
   __shared__ float sup_x[kMrExactCols];
   __shared__ int sup_n;
+  pdl_wait();
+  pdl_trigger();
   const int items = *cnt * S, tid = threadIdx.x;
   for (int item = blockIdx.x; item < items; item += gridDim.x) {   // (listed instance, column range)
     const int b = list[item / S], s = item % S;
@@ -592,6 +596,8 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_l(float* KD, int splits, 
                                                          int p, int k, MrState* st, SolveParams prm,
                                                          gpl1_result* res, int* done_count) {
   const int b = blockIdx.x, tid = threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
   MrState& S = st[b];
   __shared__ Scratch sc;
   __shared__ int flag[2];
@@ -834,19 +840,16 @@ cudaError_t launch_mr_phase_p(const float* G, const float* Gprev, const float* X
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  mr_phase_p<<<nrhs, kConsumers, mr_smem_bytes(p, 2), s>>>(G, Gprev, X, ldx, D, DXs, p, nrhs, k,
-                                                          static_cast<MrState*>(states), prm,
-                                                          MrRestartList{restart_cnt, restart_list});
-  return cudaGetLastError();
+  return launch_pdl(mr_phase_p, dim3(nrhs), dim3(kConsumers), mr_smem_bytes(p, 2), s, G, Gprev, X, ldx, D, DXs, p,
+                    nrhs, k, static_cast<MrState*>(states), prm, MrRestartList{restart_cnt, restart_list});
 }
 cudaError_t launch_mr_phase_l(float* KD, int splits, long long split_stride, const void* xpart, const float* Y,
                               long long ldy, float* X, long long ldx, const float* D, uint16_t* Rs, int n, int p,
                               int nrhs, int k, void* states, const SolveParams& prm, gpl1_result* res,
                               int* done_count, cudaStream_t s) {
-  mr_phase_l<<<nrhs, kConsumers, 0, s>>>(KD, splits, split_stride, static_cast<const F2*>(xpart), mr_exact_splits(p),
-                                         Y, ldy, X, ldx, D, Rs, n, p, k, static_cast<MrState*>(states), prm, res,
-                                         done_count);
-  return cudaGetLastError();
+  return launch_pdl(mr_phase_l, dim3(nrhs), dim3(kConsumers), 0, s, KD, splits, split_stride,
+                    static_cast<const F2*>(xpart), mr_exact_splits(p), Y, ldy, X, ldx, D, Rs, n, p, k,
+                    static_cast<MrState*>(states), prm, res, done_count);
 }
 size_t mr_exact_part_bytes(int n, int p, int nrhs) {
   return static_cast<size_t>(nrhs) * mr_exact_splits(p) * n * sizeof(F2);
@@ -856,10 +859,9 @@ cudaError_t launch_mr_exact_kx(const void* Kt, const float* X, long long ldx, vo
                                cudaStream_t s) {
   // persistent over the (listed instance, column range) items of this iteration
   const int grid = std::min(3 * num_sms, nrhs * mr_exact_splits(p));
-  mr_exact_kx<<<grid, kMrExactThreads, 0, s>>>(static_cast<const uint16_t*>(Kt), X, ldx, static_cast<F2*>(xpart), n,
-                                               p, mr_exact_splits(p), static_cast<const MrState*>(states),
-                                               restart_cnt + (k & 1), restart_list + (k & 1) * nrhs);
-  return cudaGetLastError();
+  return launch_pdl(mr_exact_kx, dim3(grid), dim3(kMrExactThreads), 0, s, static_cast<const uint16_t*>(Kt), X, ldx,
+                    static_cast<F2*>(xpart), n, p, mr_exact_splits(p), static_cast<const MrState*>(states),
+                    restart_cnt + (k & 1), restart_list + (k & 1) * nrhs);
 }
 cudaError_t launch_transpose_bf16(const void* K, long long ldk, void* Kt, int n, int p, cudaStream_t s) {
   const dim3 grid((p + 31) / 32, (n + 31) / 32), block(32, 8);
