@@ -195,6 +195,20 @@ gpl1_status gpl1_plan_create(gpl1_ctx* ctx, const gpl1_problem* probs, int count
 gpl1_status gpl1_plan_run(gpl1_plan* plan, gpl1_result* res);
 void gpl1_plan_destroy(gpl1_plan* plan);
 
+/* gpl1_solve and gpl1_solve_batched without host synchronisation: the
+ * argument checks, workspace sizing and descriptor staging happen in the call,
+ * everything else is enqueued on the context's stream, and the results (one
+ * per instance, in the order of probs; kernel_ms reads 0) are written to
+ * res_dev, a DEVICE array, when the solve completes.  The workspace is the
+ * context's: successive calls on one context are ordered by its stream, so a
+ * caller overlaps solves with its own copies on other streams (events), not
+ * with other solves of the same context.  Status codes report argument and
+ * launch errors only; an instance's outcome is in its result. */
+gpl1_status gpl1_solve_async(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype k_dtype,
+                             const gpl1_params* prm, gpl1_result* res_dev);
+gpl1_status gpl1_solve_batched_async(gpl1_ctx* ctx, const gpl1_problem* probs, int count,
+                                     gpl1_dtype k_dtype, const gpl1_params* prm, gpl1_result* res_dev);
+
 /* Tensor-core product used by the shared-K form of the method (many
  * right-hand sides on one K turn K^T r and K d into matrix products):
  *   out[n * ldo + m] = scale * sum_{k < Kd} A[m * lda + (k mod Ka)] * B[n * ldb + k]

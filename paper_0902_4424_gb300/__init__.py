@@ -31,7 +31,8 @@ ALGORITHMIC = (0, 3, 4, 5, 6)
 EXPORTS = ["gpl1_create", "gpl1_destroy", "gpl1_set_stream", "gpl1_last_error", "gpl1_params_default",
            "gpl1_project", "gpl1_solve", "gpl1_solve_batched", "gpl1_solve_noalloc", "gpl1_gemm_bf16",
            "gpl1_gemm_bf16_ex", "gpl1_gemm_tuned", "gpl1_gemm_tuned_set", "gpl1_solve_shared_k", "gpl1_lista_forward",
-           "gpl1_lista_grad", "gpl1_lista_train", "gpl1_plan_create", "gpl1_plan_run", "gpl1_plan_destroy"]
+           "gpl1_lista_grad", "gpl1_lista_train", "gpl1_plan_create", "gpl1_plan_run", "gpl1_plan_destroy",
+           "gpl1_solve_async", "gpl1_solve_batched_async"]
 
 
 class Gpl1Error(RuntimeError):
@@ -95,6 +96,10 @@ def lib():
         L.gpl1_gemm_bf16.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
                                      ctypes.c_longlong, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_float]
+        L.gpl1_solve_async.argtypes = [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.c_int,
+                                       ctypes.POINTER(Params), ctypes.c_void_p]
+        L.gpl1_solve_batched_async.argtypes = [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(Params), ctypes.c_void_p]
         L.gpl1_plan_create.argtypes = [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]
         L.gpl1_plan_run.argtypes = [ctypes.c_void_p, ctypes.POINTER(Result)]
@@ -371,6 +376,28 @@ class Context:
         self._bind_stream()
         self._check(lib().gpl1_plan_create(self._h, arr, count, dtype, ctypes.byref(prm), ctypes.byref(h)))
         return BatchedPlan(self, h, count)
+
+    def solve_batched_async(self, problems: Sequence[Problem], dtype: int, params: Params | None = None, res=None):
+        """gpl1_solve_batched_async: enqueue on PyTorch's current stream without waiting.
+        res: a uint8 device tensor of count * sizeof(Result) bytes (allocated when None);
+        returns it.  Result.from_buffer_copy on res.cpu().numpy() reads the results."""
+        import torch
+        count = len(problems)
+        arr = (Problem * count)(*problems)
+        prm = params_default() if params is None else params
+        if res is None:
+            res = torch.empty(count * ctypes.sizeof(Result), dtype=torch.uint8, device="cuda")
+        self._bind_stream()
+        self._check(lib().gpl1_solve_batched_async(self._h, arr, count, dtype, ctypes.byref(prm),
+                                                   ctypes.c_void_p(res.data_ptr())))
+        return res
+
+    @staticmethod
+    def results_from_device(res, count: int):
+        """Results written by an asynchronous solve (a uint8 device tensor) as Result objects."""
+        raw = bytes(res.cpu().numpy().tobytes())
+        size = ctypes.sizeof(Result)
+        return [Result.from_buffer_copy(raw[i * size:(i + 1) * size]) for i in range(count)]
 
     def solve_batched(self, problems: Sequence[Problem], dtype: int, params: Params | None = None):
         """Solve independent instances in one persistent launch (gpl1_solve_batched); returns results."""

@@ -363,7 +363,7 @@ gpl1_status stage_batch(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int
 gpl1_status enqueue_batch(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
                           const BatchLayout& L, uint8_t* ws, const uint8_t* host, const CUtensorMap& tmap0,
                           cudaStream_t stream, gpl1_result* host_res, cudaEvent_t ev0, cudaEvent_t ev1,
-                          bool capture = false) {
+                          bool capture = false, cudaMemcpyKind res_kind = cudaMemcpyDeviceToHost) {
   // under stream capture the events become event-record nodes of the graph
   const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (prm->x0_is_zero)   // x0 = 0: the iterate buffer must start at zero
@@ -400,7 +400,7 @@ gpl1_status enqueue_batch(gpl1_ctx* ctx, const gpl1_problem* probs, int count, i
     GPL1_CUDA(launch_gpss(dt, ka, tmap0, grid, false, stream), "solver launch");
   }
   GPL1_CUDA(cudaEventRecordWithFlags(ev1, stream, evf), "cudaEventRecord");
-  GPL1_CUDA(cudaMemcpyAsync(host_res, ws + L.off_res, sizeof(gpl1_result) * count, cudaMemcpyDeviceToHost, stream),
+  GPL1_CUDA(cudaMemcpyAsync(host_res, ws + L.off_res, sizeof(gpl1_result) * count, res_kind, stream),
             "cudaMemcpyAsync(result)");
   return GPL1_OK;
 }
@@ -417,6 +417,26 @@ gpl1_status finish_batch(gpl1_ctx* ctx, int count, const gpl1_result* host_res, 
     if (res[q].status != GPL1_OK && res[q].status != GPL1_ERR_NOT_CONVERGED) worst = res[q].status;
   if (worst != GPL1_OK) return fail(ctx, static_cast<gpl1_status>(worst), "an instance failed (status %d)", worst);
   return GPL1_OK;
+}
+
+// Enqueue only: the results go to res_dev (device memory), nothing waits.
+gpl1_status run_async(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
+                      gpl1_result* res_dev) {
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const BatchLayout L = batch_layout(ctx, probs, count, dt);
+  gpl1_status st = ensure_ws(ctx, L.total);
+  if (st) return st;
+  uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
+  ctx->host_stage.assign(L.off_bufs - L.off_desc, 0);   // pageable: copied before cudaMemcpyAsync returns
+  CUtensorMap tmap0;
+  st = stage_batch(ctx, probs, count, dt, prm, L, ws, ctx->host_stage.data(), &tmap0);
+  if (st) return st;
+  if (!ctx->ev[0]) {
+    GPL1_CUDA(cudaEventCreate(&ctx->ev[0]), "cudaEventCreate");
+    GPL1_CUDA(cudaEventCreate(&ctx->ev[1]), "cudaEventCreate");
+  }
+  return enqueue_batch(ctx, probs, count, dt, prm, L, ws, ctx->host_stage.data(), tmap0, ctx->stream, res_dev,
+                       ctx->ev[0], ctx->ev[1], false, cudaMemcpyDeviceToDevice);
 }
 
 gpl1_status run(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
@@ -455,6 +475,32 @@ gpl1_status gpl1_solve(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype dt, c
   st = check_problem(ctx, prob, dt, 0);
   if (st) return st;
   return run(ctx, prob, 1, dt, prm, res);
+}
+
+gpl1_status gpl1_solve_async(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype dt, const gpl1_params* prm,
+                             gpl1_result* res_dev) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  if (dt != GPL1_F64 && dt != GPL1_F32 && dt != GPL1_BF16) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad dtype");
+  if (!res_dev) return fail(ctx, GPL1_ERR_INVALID_ARG, "result is NULL");
+  gpl1_status st = check_params(ctx, prm);
+  if (st) return st;
+  st = check_problem(ctx, prob, dt, 0);
+  if (st) return st;
+  return run_async(ctx, prob, 1, dt, prm, res_dev);
+}
+
+gpl1_status gpl1_solve_batched_async(gpl1_ctx* ctx, const gpl1_problem* probs, int count, gpl1_dtype dt,
+                                     const gpl1_params* prm, gpl1_result* res_dev) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  if (dt != GPL1_F64 && dt != GPL1_F32 && dt != GPL1_BF16) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad dtype");
+  if (!probs || !res_dev || count < 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "need probs, res and count >= 1");
+  gpl1_status st = check_params(ctx, prm);
+  if (st) return st;
+  for (int q = 0; q < count; ++q) {
+    st = check_problem(ctx, &probs[q], dt, q);
+    if (st) return st;
+  }
+  return run_async(ctx, probs, count, dt, prm, res_dev);
 }
 
 gpl1_status gpl1_solve_batched(gpl1_ctx* ctx, const gpl1_problem* probs, int count, gpl1_dtype dt,

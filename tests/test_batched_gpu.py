@@ -105,3 +105,48 @@ def test_batched_plan_replays_the_batched_solve(gpu_ctx):
         assert torch.equal(x, xn)
         assert (r.status, r.iters, r.f) == (rr.status, rr.iters, rr.f)
     plan.close()
+
+
+def test_async_solves_match_the_synchronous_ones(gpu_ctx):
+    """gpl1_solve_batched_async / gpl1_solve_async: enqueued without waiting, results
+    in device memory, the same iterates and results as the synchronous calls; the
+    stream orders two asynchronous solves on one context."""
+    import ctypes
+    rng = np.random.default_rng(9)
+    sizes = [int(v) for v in rng.integers(40, 260, size=6)]
+    probs = [W.gaussian(n, 4 * n, max(1, n // 20), dtype=W.DT_F32, seed=3000 + i, law="pm1")
+             for i, n in enumerate(sizes)]
+    keep = [upload(pr) for pr in probs]
+    descs = [pkg.Context.make_problem(K, y, pr.rho, x, pr.p) for (K, y, x), pr in zip(keep, probs)]
+    prm = pkg.params_default(stop_rule=0, x0_is_zero=1, max_iter=30)
+    ref = gpu_ctx.solve_batched(descs, W.DT_F32, prm)
+    torch.cuda.synchronize()
+    x_ref = [x.clone() for _, _, x in keep]
+    for _, _, x in keep:
+        x.fill_(5.0)
+    r1 = gpu_ctx.solve_batched_async(descs, W.DT_F32, prm)
+    x_mid = [x.clone() for _, _, x in keep]      # stream-ordered after the first solve
+    r2 = gpu_ctx.solve_batched_async(descs, W.DT_F32, prm)
+    torch.cuda.synchronize()
+    for res in (r1, r2):
+        got = pkg.Context.results_from_device(res, len(descs))
+        for g, rr in zip(got, ref):
+            assert (g.status, g.iters, g.f, g.backtracks) == (rr.status, rr.iters, rr.f, rr.backtracks)
+    for (_, _, x), xm, xr in zip(keep, x_mid, x_ref):
+        assert torch.equal(x, xr) and torch.equal(xm, xr)
+    # the single-instance form, against the synchronous single solve
+    K, y, x = keep[0]
+    x1, r1s = gpu_ctx.solve(K, y, probs[0].rho, x=x.clone(), p=probs[0].p, params=prm)
+    torch.cuda.synchronize()
+    res = torch.empty(ctypes.sizeof(pkg.Result), dtype=torch.uint8, device=DEV)
+    pr = pkg.Context.make_problem(K, y, probs[0].rho, x, probs[0].p)
+    st = pkg.lib().gpl1_solve_async(gpu_ctx._h, ctypes.byref(pr), W.DT_F32, ctypes.byref(prm),
+                                    ctypes.c_void_p(res.data_ptr()))
+    assert st == 0
+    torch.cuda.synchronize()
+    g = pkg.Context.results_from_device(res, 1)[0]
+    # a multi-CTA solve adds its partial products with float atomics, so two runs
+    # agree to rounding, not bit for bit
+    assert (g.status, g.iters) == (r1s.status, r1s.iters)
+    assert abs(g.f - r1s.f) <= 1e-6 * r1s.f
+    assert torch.linalg.norm(x - x1) <= 1e-4 * torch.linalg.norm(x1)
