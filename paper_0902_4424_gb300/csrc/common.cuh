@@ -107,6 +107,30 @@ __device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+// Warp sum of NV values at once (NV a power of two, at most 32): at each of the
+// first log2 NV butterfly levels a lane keeps half of its values and adds the
+// partner's copy of that half, so the warp exchanges NV - 1 + (5 - log2 NV)
+// values instead of 5 NV.  On return every lane of the group of 32 / NV lanes
+// starting at lane q * (32 / NV) holds the warp total of v[q].
+template <int NV>
+__device__ __forceinline__ float warp_sum_many(float (&v)[NV], int lane) {
+  static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV must be a power of two <= 32");
+  int o = 16;
+#pragma unroll
+  for (int n = NV; n > 1; n >>= 1, o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const float send = upper ? v[i] : v[i + n / 2];
+      const float keep = upper ? v[i + n / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  return v[0];
+}
+
 // Programmatic dependent launch: a kernel launched with the programmatic
 // stream-serialization attribute may start (block scheduling, prologue) while
 // its predecessor in the stream still runs; pdl_wait() blocks until the

@@ -548,6 +548,33 @@ struct Consumer {
         skip();
         continue;
       }
+      if constexpr (!kF64 && !acc) {
+        // far from the stop, plain FP32 sums: the warp's RPW rows x (K d, K x)
+        // reduced together (warp_sum_many), then one v2 add per row
+        float vals[2 * RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          A kv[8];
+          load_row8<DT>(st + (warp + kConsumerWarps * q) * (kBoxCols * T::ES), lane, kv);
+          float pd = 0.f, sh = 0.f;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            pd = fmaf(kv[e], dv[e], pd);
+            sh = fmaf(kv[e], xv[e], sh);
+          }
+          vals[2 * q] = pd;
+          vals[2 * q + 1] = sh;
+        }
+        const float tot = warp_sum_many<2 * RPW>(vals, lane);   // lane q * GL holds value q
+        constexpr int GL = 32 / (2 * RPW);
+        const float kx_tot = __shfl_down_sync(0xffffffffu, tot, GL);
+        if (lane % (2 * GL) == 0) {
+          const int i = b * RB + warp + kConsumerWarps * (lane / (2 * GL));
+          if (i < n) red_add2(kp + 2 * i, tot, kx_tot);
+        }
+        release();
+        continue;
+      }
 #pragma unroll
       for (int q = 0; q < RPW; ++q) {
         A kv[8];
