@@ -261,6 +261,36 @@ __device__ __forceinline__ F2 f2_fma(F2 acc, float a, float b) {   // acc + a*b,
   return two_sum(s.hi, s.lo);
 }
 
+// warp_sum_many for float pairs: the same halving butterfly, each combine an
+// error-free two-sum of the high words with the low words and the rounding
+// error added to the low word.
+template <int NV>
+__device__ __forceinline__ F2 warp_sum_many_f2(F2 (&v)[NV], int lane) {
+  static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV must be a power of two <= 32");
+  int o = 16;
+#pragma unroll
+  for (int n = NV; n > 1; n >>= 1, o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const F2 send = upper ? v[i] : v[i + n / 2];
+      const F2 keep = upper ? v[i + n / 2] : v[i];
+      const float oh = __shfl_xor_sync(0xffffffffu, send.hi, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, send.lo, o);
+      const F2 t = two_sum(keep.hi, oh);
+      v[i] = F2{t.hi, __fadd_rn(__fadd_rn(keep.lo, ol), t.lo)};
+    }
+  }
+#pragma unroll
+  for (; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, v[0].hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, v[0].lo, o);
+    const F2 t = two_sum(v[0].hi, oh);
+    v[0] = F2{t.hi, __fadd_rn(__fadd_rn(v[0].lo, ol), t.lo)};
+  }
+  return v[0];
+}
+
 struct Scratch {
   double d[kConsumerWarps][8];   // per-warp partials of block reductions (FP64 data)
   F2 f2[kConsumerWarps][8];      // per-warp partials of block reductions (float data)

@@ -575,6 +575,41 @@ struct Consumer {
         release();
         continue;
       }
+      if constexpr (!kF64 && acc) {
+        // near the stop, K x without rounding error: the rows' (K d, K x) reduced
+        // together as above, K x as exact float pairs (warp_sum_many_f2)
+        float vd[RPW];
+        F2 vx[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          A kv[8];
+          load_row8<DT>(st + (warp + kConsumerWarps * q) * (kBoxCols * T::ES), lane, kv);
+          float pd = 0.f, sh = 0.f, sl = 0.f;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            pd = fmaf(kv[e], dv[e], pd);
+            const float pr = __fmul_rn(kv[e], xv[e]);
+            const float pe = fmaf(kv[e], xv[e], -pr);   // K_ij x_j - pr, exact
+            const F2 t = two_sum(sh, pr);
+            sh = t.hi;
+            sl = __fadd_rn(sl, __fadd_rn(pe, t.lo));
+          }
+          vd[q] = pd;
+          vx[q] = F2{sh, sl};
+        }
+        const float dtot = warp_sum_many<RPW>(vd, lane);       // lane q * GL holds row q
+        const F2 xtot = warp_sum_many_f2<RPW>(vx, lane);
+        constexpr int GL = 32 / RPW;
+        if (lane % GL == 0) {
+          const int i = b * RB + warp + kConsumerWarps * (lane / GL);
+          if (i < n) {
+            red_add(kp + 2 * i, dtot);
+            red_add(kx64 + i, static_cast<double>(xtot.hi) + static_cast<double>(xtot.lo));
+          }
+        }
+        release();
+        continue;
+      }
 #pragma unroll
       for (int q = 0; q < RPW; ++q) {
         A kv[8];
