@@ -81,3 +81,18 @@ def test_gemm_ex_rejects_bad_config(gpu_ctx):
         with pytest.raises(pkg.Gpl1Error) as e:
             gpu_ctx.gemm_bf16_ex(A, B, cfg, spl)
         assert e.value.status == 1
+
+
+@pytest.mark.parametrize("M,N", [(1, 1), (1, 300), (300, 1)])
+def test_gemm_degenerate_output_shapes(gpu_ctx, M, N):
+    """One output row or column: a single partial tile, every other row/column masked."""
+    rng = np.random.default_rng(M * 1000 + N)
+    a_bits, a = bf16(rng, (M, 128))
+    b_bits, b = bf16(rng, (N, 128))
+    A = torch.from_numpy(a_bits.view(np.int16)).to(DEV)
+    B = torch.from_numpy(b_bits.view(np.int16)).to(DEV)
+    out = gpu_ctx.gemm_bf16(A, B)
+    torch.cuda.synchronize()
+    exact = b @ a.T
+    bound = 128 * 2.0 ** -23 * (np.abs(b) @ np.abs(a).T) + 1e-30
+    assert np.all(np.abs(out.double().cpu().numpy() - exact) <= bound)

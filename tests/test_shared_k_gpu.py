@@ -175,3 +175,20 @@ def test_radius_sweep_shared_and_continuation():
         assert r.status == 0
         assert (oracle.objective(prob, x.double().cpu().numpy()) - fstars[q]) / fstars[q] <= 1e-6, q
     ctx.close()
+
+
+def test_shared_k_smallest_shapes():
+    """The smallest shapes the shared-K form takes: n = p = 64 and one right-hand
+    side (a single tile, the contraction one k-block of each split term)."""
+    n, p, nrhs, k = 64, 64, 1, 3
+    Ks, ldk, Y, rho, probs = instances(n, p, nrhs, k, seed=5)
+    fstar = np.array([oracle.reference_solve(pr)[1].f for pr in probs])
+    ctx = pkg.Context(0)
+    K = torch.from_numpy(Ks.view(np.int16)).to(DEV)
+    Yd = torch.from_numpy(Y).to(DEV)
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, max_iter=3000)
+    X, res = ctx.solve_shared_k(K, Yd, rho, p=p, f_star=fstar, params=prm)
+    torch.cuda.synchronize()
+    assert res[0].status == 0, res[0].as_dict()
+    assert (oracle.objective(probs[0], X[0].double().cpu().numpy()) - fstar[0]) / fstar[0] <= 1e-6
+    ctx.close()
