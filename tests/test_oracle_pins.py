@@ -424,3 +424,57 @@ def test_nonmonotone_line_search_invariant():
     for k in range(1, len(f)):
         assert f[k] < max(f[max(0, k - M):k]) or f[k] == f[k - 1] == 0.0
     assert np.abs(x).sum() <= prob.rho * (1 + 1e-12)
+
+
+# ------------------------------------------------------- homotopy path (exact)
+from oracle import homotopy  # noqa: E402
+
+
+@pytest.mark.parametrize("seed,n,p,k", [(0, 30, 60, 6), (1, 30, 60, 6), (2, 40, 120, 8), (3, 50, 40, 5),
+                                        (4, 20, 200, 4), (5, 64, 64, 10)])
+def test_oracle_matches_the_exact_homotopy_path(seed, n, p, k):
+    """The homotopy (LARS-Lasso) path gives the minimiser of eq. 2 without iterating:
+    it satisfies the optimality conditions of Sec. 1 to rounding (c = K^T (y - K x)
+    equals lam sgn x on the support, |c| <= lam off it, ||x||_1 = rho), and the
+    oracle's Alg. GP + SS solution agrees with it: the same support and signs, x to
+    1e-6, f and lam to 1e-8 (the oracle, after tens of thousands of iterations at its
+    floor, sits within about 1e-11 relative of the ball's surface)."""
+    rng = np.random.default_rng(seed)
+    K = rng.standard_normal((n, p)) / np.sqrt(n)
+    xt = np.zeros(p)
+    xt[rng.choice(p, k, replace=False)] = rng.standard_normal(k)
+    y = K @ xt + 0.01 * rng.standard_normal(n)
+    rho = 0.8 * np.abs(xt).sum()
+    xh, lam, segs = homotopy.solve_at_radius(K, y, rho)
+    assert segs >= 1
+    c = K.T @ (y - K @ xh)
+    on = xh != 0
+    assert abs(np.abs(xh).sum() - rho) <= 1e-12 * rho
+    assert np.max(np.abs(c[on] - lam * np.sign(xh[on]))) <= 1e-12 * lam
+    assert np.max(np.abs(c[~on])) <= lam * (1 + 1e-12)
+    prob = W.Problem(np.ascontiguousarray(K), n, p, p, W.DT_F64, y, rho, xt, "homotopy")
+    xo, ro, _ = oracle.reference_solve(prob)
+    assert np.array_equal(np.sign(xh), np.sign(np.where(np.abs(xo) > 1e-9 * np.abs(xo).max(), xo, 0.0)))
+    assert np.linalg.norm(xo - xh) <= 1e-6 * np.linalg.norm(xh)
+    fh = float(np.sum((K @ xh - y) ** 2))
+    assert abs(ro.f - fh) <= 1e-8 * fh
+    assert abs(ro.lambda_reg - lam) <= 1e-6 * lam
+
+
+def test_homotopy_path_is_piecewise_linear_and_monotone():
+    """Along the path ||x(lam)||_1 grows as lam falls, and between two radii on one
+    segment (same support and signs) the solution is the linear interpolation."""
+    rng = np.random.default_rng(11)
+    n, p = 30, 80
+    K = rng.standard_normal((n, p)) / np.sqrt(n)
+    xt = np.zeros(p)
+    xt[rng.choice(p, 7, replace=False)] = rng.standard_normal(7)
+    y = K @ xt + 0.01 * rng.standard_normal(n)
+    radii = np.linspace(0.05, 0.9, 40) * np.abs(xt).sum()
+    sols = [homotopy.solve_at_radius(K, y, r) for r in radii]
+    lams = np.array([s[1] for s in sols])
+    assert np.all(np.diff(lams) < 0)
+    for (x0, _, _), (x1, _, _), (x2, _, _), r0, r1, r2 in zip(sols, sols[1:], sols[2:], radii, radii[1:], radii[2:]):
+        if np.array_equal(np.sign(x0), np.sign(x1)) and np.array_equal(np.sign(x1), np.sign(x2)):
+            t = (r1 - r0) / (r2 - r0)
+            assert np.linalg.norm(x1 - ((1 - t) * x0 + t * x2)) <= 1e-10 * np.linalg.norm(x1)
