@@ -21,7 +21,11 @@ Tibshirani 2004, the Lasso modification of LARS):
     ||x||_1 = rho is found exactly.
 
 Each step is a small dense solve; the path is exact up to the rounding of those
-solves (it assumes general position: one event at a time).
+solves (it assumes general position: one event at a time).  An index that just
+joined may not leave on the next segment, nor one that just left join again
+(rounding would otherwise produce a step of length ~0 the wrong way), and the
+result is checked against the optimality conditions before it is returned: a
+path lost to rounding raises instead of returning a wrong point.
 """
 from __future__ import annotations
 
@@ -41,6 +45,7 @@ def solve_at_radius(K, y, rho: float, max_segments: int = 10000):
     if lam == 0.0 or rho <= 0.0:
         return x, lam, 0
     active = [int(np.argmax(np.abs(c)))]
+    just_joined, just_left = active[0], -1
     for seg in range(1, max_segments + 1):
         A = np.array(active)
         s = np.sign(c[A])
@@ -53,32 +58,49 @@ def solve_at_radius(K, y, rho: float, max_segments: int = 10000):
         gamma, event = lam, ("end", -1)  # lam cannot drop below 0
         inactive = np.setdiff1d(np.arange(p), A)
         for j in inactive:
+            if j == just_left:
+                continue
             for sgn in (1.0, -1.0):      # c_j - gamma a_j = sgn (lam - gamma)
                 den = sgn - a[j]
                 if den != 0.0:
                     g = (sgn * lam - c[j]) / den
-                    if 1e-15 * lam < g < gamma:
+                    if 0.0 < g < gamma:
                         gamma, event = g, ("join", int(j))
         for q, j in enumerate(A):
-            if delta[q] != 0.0:
+            if delta[q] != 0.0 and j != just_joined:
                 g = -x[j] / delta[q]
-                if 1e-15 * lam < g < gamma:
+                if 0.0 < g < gamma:
                     gamma, event = g, ("leave", int(j))
         # does ||x||_1 reach rho on this segment?
         if dl1 > 0.0 and l1 + gamma * dl1 >= rho:
             g = (rho - l1) / dl1
             x[A] += g * delta
-            return x, lam - g, seg
+            return _checked(K, y, x, lam - g), lam - g, seg
         x[A] += gamma * delta
         c = c - gamma * a
         lam -= gamma
+        just_joined, just_left = -1, -1
         if event[0] == "join":
             active.append(event[1])
+            just_joined = event[1]
         elif event[0] == "leave":
             active.remove(event[1])
             x[event[1]] = 0.0
+            just_left = event[1]
         else:   # lam reached 0: the least-squares end of the path
             return x, 0.0, seg
         if len(active) > min(n, p):
             return x, lam, seg
     raise RuntimeError("homotopy did not reach the radius")
+
+
+def _checked(K, y, x, lam):
+    """x if it meets the optimality conditions at lam (c = K^T (y - K x) equals
+    lam sgn x on the support, |c| <= lam off it, both to 1e-9 of lam); raises otherwise."""
+    c = K.T @ (y - K @ x)
+    on = x != 0
+    if on.any() and np.max(np.abs(c[on] - lam * np.sign(x[on]))) > 1e-9 * lam:
+        raise RuntimeError("homotopy: the path was lost (support conditions)")
+    if (~on).any() and np.max(np.abs(c[~on])) > lam * (1 + 1e-9):
+        raise RuntimeError("homotopy: the path was lost (an inactive correlation exceeds lam)")
+    return x

@@ -222,24 +222,3 @@ def test_nonmonotone_line_search_matches_oracle(gpu_ctx):
     x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000, M=10)
     assert res.status == 0, res.as_dict()
     assert rel_gap(prob, x, rs.f) <= 1e-6
-
-
-@pytest.mark.parametrize("seed,n,p,k", [(0, 30, 60, 6), (2, 40, 120, 8), (5, 64, 64, 10)])
-def test_fp64_solve_matches_the_exact_homotopy_path(gpu_ctx, seed, n, p, k):
-    """The FP64 path against the exact minimiser from the homotopy path (no iteration
-    on the reference side): the same support and signs, x to 1e-6, f to 1e-9."""
-    from oracle import homotopy
-    rng = np.random.default_rng(seed)
-    K = rng.standard_normal((n, p)) / np.sqrt(n)
-    xt = np.zeros(p)
-    xt[rng.choice(p, k, replace=False)] = rng.standard_normal(k)
-    y = K @ xt + 0.01 * rng.standard_normal(n)
-    rho = 0.8 * np.abs(xt).sum()
-    xh, lam, _ = homotopy.solve_at_radius(K, y, rho)
-    fh = float(np.sum((K @ xh - y) ** 2))
-    prob = W.Problem(np.ascontiguousarray(K), n, p, p, W.DT_F64, y, rho, xt, "homotopy")
-    x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=1e-12, f_star=fh, max_iter=100000)
-    assert res.status == 0, res.as_dict()
-    assert abs(oracle.objective(prob, x) - fh) <= 1e-9 * fh
-    assert np.linalg.norm(x - xh) <= 1e-6 * np.linalg.norm(xh)
-    assert np.array_equal(np.sign(xh), np.sign(np.where(np.abs(x) > 1e-9 * np.abs(x).max(), x, 0.0)))
