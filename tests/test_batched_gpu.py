@@ -170,3 +170,44 @@ def test_plan_of_a_single_instance(gpu_ctx):
         assert r.status == 0 and r.stop == 0, r.as_dict()
         assert (oracle.objective(prob, x.double().cpu().numpy()) - fs) / fs <= 1e-6
     plan.close()
+
+
+def test_batched_degenerate_instances(gpu_ctx):
+    """A batch (FP64) mixing the degenerate cases with ordinary ones: y = 0 (x0 = 0 is
+    stationary at once), a radius above ||x_LS||_1 (the constraint inactive: the
+    least-squares solution), n = 1, and two ordinary instances."""
+    rng = np.random.default_rng(21)
+    probs, fstars = [], []
+    zero = W.gaussian(40, 160, 4, dtype=W.DT_F64, seed=31)
+    zero.y[:] = 0.0
+    probs.append(zero)
+    fstars.append(0.0)
+    n, p = 120, 40                                  # inactive constraint
+    K = rng.standard_normal((n, p)) / np.sqrt(n)
+    y = rng.standard_normal(n)
+    x_ls = np.linalg.lstsq(K, y, rcond=None)[0]
+    probs.append(W.Problem(np.ascontiguousarray(K), n, p, p, W.DT_F64, y, 10 * np.abs(x_ls).sum(), x_ls, "ls"))
+    fstars.append(float(np.sum((K @ x_ls - y) ** 2)))
+    for pr in (W.gaussian(1, 40, 1, dtype=W.DT_F64, seed=32, rho_scale=0.5),
+               W.gaussian(60, 240, 6, dtype=W.DT_F64, seed=33), W.gaussian(200, 800, 10, dtype=W.DT_F64, seed=34)):
+        probs.append(pr)
+        fstars.append(oracle.reference_solve(pr)[1].f)
+    keep = [upload(pr) for pr in probs]
+    descs = [pkg.Context.make_problem(Kd, yd, pr.rho, x, pr.p, fs if fs > 0 else -1.0)
+             for (Kd, yd, x), pr, fs in zip(keep, probs, fstars)]
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=1e-10, x0_is_zero=1, max_iter=100000)
+    res = gpu_ctx.solve_batched(descs, W.DT_F64, prm)
+    torch.cuda.synchronize()
+    xs = [x.double().cpu().numpy() for _, _, x in keep]
+    assert res[0].stop == 1 and res[0].iters == 0 and np.all(xs[0] == 0)          # stationary at x0 = 0
+    assert res[1].status == 0
+    # least squares: a 1e-10 gap on f* bounds ||K dx|| by about 1e-4, so |dx| <~ 3e-4
+    np.testing.assert_allclose(xs[1], x_ls, atol=1e-3)
+    # n = 1 fits y almost exactly (f* ~ 0): the relative-gap stop may not be reachable and
+    # the instance runs to max_iter (status 3); its objective is checked all the same
+    for q in (2, 3, 4):
+        assert res[q].status in (0, 3), (q, res[q].as_dict())
+        f = oracle.objective(probs[q], xs[q])
+        bar = 1e-8 if q == 2 else 1e-6
+        assert f - fstars[q] <= bar * fstars[q] + 1e-14, q
+        assert np.abs(xs[q]).sum() <= probs[q].rho * (1 + 1e-9)
