@@ -28,7 +28,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBDIR = os.path.join(_HERE, "lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
-_SRC = [os.path.join(_HERE, "gpss_oracle.c"), os.path.join(_HERE, "lista_oracle.c")]
+_SRC = [os.path.join(_HERE, "gpss_oracle.c")]
 
 STOP_NAMES = {0: "rel_gap", 1: "stationary", 2: "fw", 3: "max_iter", 4: "linesearch",
               5: "nonfinite", 6: "stagnation"}
@@ -37,7 +37,7 @@ STOP_NAMES = {0: "rel_gap", 1: "stationary", 2: "fw", 3: "max_iter", 4: "linesea
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (portable C, OpenMP; no target-specific flags)."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    srcs = [s for s in _SRC if os.path.exists(s)]
+    srcs = list(_SRC)
     newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "gpss_oracle.h")])
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"

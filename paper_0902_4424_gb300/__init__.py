@@ -149,9 +149,18 @@ def _dtype_code(t) -> int:
     raise TypeError(f"unsupported K dtype {t.dtype}")
 
 
-def _stream_handle():
+def _stream_handle(device=None):
     import torch
-    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _same_device(device, *tensors):
+    """Raise unless every tensor lives on CUDA device index `device`."""
+    for t in tensors:
+        if t is None:
+            continue
+        if not t.is_cuda or t.device.index != device:
+            raise ValueError(f"tensor on {t.device}, expected cuda:{device}")
 
 
 class Context:
@@ -163,7 +172,7 @@ class Context:
             raise RuntimeError("gpl1 needs a CUDA GPU")
         self.device = torch.cuda.current_device() if device is None else int(device)
         h = ctypes.c_void_p()
-        st = lib().gpl1_create(ctypes.byref(h), self.device, _stream_handle())
+        st = lib().gpl1_create(ctypes.byref(h), self.device, _stream_handle(self.device))
         if st != 0:
             raise Gpl1Error(st, "gpl1_create failed")
         self._h = h
@@ -184,7 +193,8 @@ class Context:
             raise Gpl1Error(st, lib().gpl1_last_error(self._h).decode())
 
     def _bind_stream(self):
-        lib().gpl1_set_stream(self._h, _stream_handle())
+        """Bind the context to PyTorch's current stream of the context's device."""
+        lib().gpl1_set_stream(self._h, _stream_handle(self.device))
 
     # ------------------------------------------------------------ project
     def project(self, v, rho, out=None, tau=None):
@@ -331,6 +341,7 @@ class Context:
             x = torch.zeros(p, dtype=vdt, device=K.device)
             prm = Params.from_buffer_copy(prm)
             prm.x0_is_zero = 1
+        _same_device(self.device, K, y, x, trace)
         pr = self.make_problem(K, y, rho, x, p, f_star, trace)
         res = Result()
         self._bind_stream()
@@ -444,8 +455,11 @@ NOALLOC_SCRATCH_BYTES = 4 << 20
 
 def solve_noalloc(K, y, rho, x=None, p=None, params: Params | None = None, f_star: float = -1.0):
     """gpl1_solve_noalloc: one solve with the library's static scratch instead of
-    a context's workspace (no allocation inside the call).  Same arguments as
-    Context.solve; enqueues on PyTorch's current stream of K's device.
+    a context's workspace (no allocation inside the C call).  Same arguments as
+    Context.solve; runs with K's device current and enqueues on PyTorch's
+    current stream of that device.  Pass a preallocated x (x0 in, solution out)
+    to keep this wrapper from allocating too; with x None it allocates a zero
+    x through PyTorch before the call.
     Returns (x, Result); raises Gpl1Error on argument, size or CUDA errors."""
     import torch
     code = _dtype_code(K)
@@ -456,11 +470,13 @@ def solve_noalloc(K, y, rho, x=None, p=None, params: Params | None = None, f_sta
         x = torch.zeros(p, dtype=torch.float64 if code == F64 else torch.float32, device=K.device)
         prm = Params.from_buffer_copy(prm)
         prm.x0_is_zero = 1
+    _same_device(K.device.index, K, y, x)
     pr = Context.make_problem(K, y, rho, x, p, f_star)
     res = Result()
     err = ctypes.create_string_buffer(256)
-    st = lib().gpl1_solve_noalloc(ctypes.byref(pr), code, ctypes.byref(prm), ctypes.byref(res), _stream_handle(),
-                                  err, len(err))
+    with torch.cuda.device(K.device):
+        st = lib().gpl1_solve_noalloc(ctypes.byref(pr), code, ctypes.byref(prm), ctypes.byref(res),
+                                      _stream_handle(K.device), err, len(err))
     if st not in ALGORITHMIC:   # argument, size and CUDA errors raise; solver outcomes are in res.status
         raise Gpl1Error(st, err.value.decode())
     return x, res

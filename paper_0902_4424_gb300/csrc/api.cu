@@ -626,7 +626,18 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[GPL1_NOALLOC_SC
 
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kNoallocMaxDevices] = {};
+// Per device: the scratch address and the CUDA context it was taken in.  A
+// cudaDeviceReset (by the caller or a framework) destroys the primary context
+// with the module; the next context loads the module again and the array may
+// sit elsewhere, so the address is looked up again whenever the current
+// context differs from the one recorded.
+struct NoallocSlot {
+  void* addr = nullptr;
+  CUcontext ctx = nullptr;
+};
+NoallocSlot g_noalloc_slot[kNoallocMaxDevices];
+using PFN_ctxGetCurrent = CUresult (*)(CUcontext*);
+PFN_ctxGetCurrent g_ctx_get_current = nullptr;
 
 gpl1_status noalloc_fail(char* err, int err_len, gpl1_status st, const char* msg) {
   if (err && err_len > 0) std::snprintf(err, static_cast<size_t>(err_len), "%s", msg);
@@ -668,17 +679,36 @@ extern "C" gpl1_status gpl1_solve_noalloc(const gpl1_problem* prob, gpl1_dtype d
     return noalloc_fail(err, err_len, GPL1_ERR_UNSUPPORTED, msg);
   }
 
-  // per-device setup, once: the scratch address (this also loads the module)
+  // per-device setup: the scratch address (the first lookup also loads the
+  // module), taken again after the device's context has been replaced
   uint8_t* ws = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (!g_ctx_get_current) {
+      cudaDriverEntryPointQueryResult q;
+      void* fn = nullptr;
+      e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q);
+      if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return noalloc_fail(err, err_len, GPL1_ERR_CUDA, "cuCtxGetCurrent is not available");
+      g_ctx_get_current = reinterpret_cast<PFN_ctxGetCurrent>(fn);
+    }
+    // make the device's primary context current (since CUDA 12 cudaSetDevice
+    // initialises it; the device is already the current one)
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return noalloc_fail(err, err_len, GPL1_ERR_CUDA, cudaGetErrorString(e));
+    CUcontext cur = nullptr;
+    if (g_ctx_get_current(&cur) != CUDA_SUCCESS || !cur)
+      return noalloc_fail(err, err_len, GPL1_ERR_CUDA, "no current CUDA context");
+    NoallocSlot& slot = g_noalloc_slot[dev];
+    if (!slot.addr || slot.ctx != cur) {
       void* a = nullptr;
       e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
-      if (e != cudaSuccess || !a) return noalloc_fail(err, err_len, GPL1_ERR_CUDA, cudaGetErrorString(e));
-      g_noalloc_addr[dev] = a;
+      if (e != cudaSuccess) return noalloc_fail(err, err_len, GPL1_ERR_CUDA, cudaGetErrorString(e));
+      if (!a) return noalloc_fail(err, err_len, GPL1_ERR_CUDA, "cudaGetSymbolAddress returned a null scratch address");
+      slot.addr = a;
+      slot.ctx = cur;
     }
-    ws = static_cast<uint8_t*>(g_noalloc_addr[dev]);
+    ws = static_cast<uint8_t*>(slot.addr);
   }
 
   CUtensorMap tmap;

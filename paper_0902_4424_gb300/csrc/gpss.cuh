@@ -1394,9 +1394,13 @@ __global__ void __launch_bounds__(kThreads, 1) gpss_kernel(const __grid_constant
     const void* tmap = D.tmap ? D.tmap : static_cast<const void*>(&tmap0);
     if (tid >= kConsumers) {
       if (tid == kConsumers) producer_run<DT>(D, tmap, sm, it, cta, G, a.prm.timeout_ns);
+      // lane 0 of the producer warp ran the producer loop alone: reconverge the
+      // warp before the aligned block barrier below
+      __syncwarp();
     } else {
       Consumer<DT> c(a, D, sm, it, epoch, cta, G);
       c.run();
+      __syncwarp();
     }
     __syncthreads();
     if (sm.ctl[CTL_BROKEN]) break;   // its barriers are in an unknown state: take no more instances

@@ -34,9 +34,23 @@ def test_noalloc_matches_context_solve(gpu_ctx, which):
     torch.cuda.synchronize()
     assert r_ref.status == 0, r_ref.as_dict()
     xr = x_ref.double().cpu().numpy()
+    # x preallocated (x0 = 0 through the parameter), so that neither the C call
+    # nor the wrapper allocates device memory during the calls below
+    prm0 = pkg.Params.from_buffer_copy(prm)
+    prm0.x0_is_zero = 1
+    x = torch.full((prob.p,), float("nan"), dtype=x_ref.dtype, device=DEV)
     for call in range(2):   # the second call reuses the static scratch
-        x, r = pkg.solve_noalloc(K, y, prob.rho, p=prob.p, params=prm)
         torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        x, r = pkg.solve_noalloc(K, y, prob.rho, x=x, p=prob.p, params=prm0)
+        torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info()[0]
+        # the entry point's defining property: it allocates nothing.  The first
+        # call may load the module that holds the static array (lazy module
+        # loading), which places the array; from the second call on, free
+        # device memory must not move.
+        if call > 0:
+            assert free_after == free_before, (call, free_before, free_after)
         assert r.status == 0 and r.stop == 0, (call, r.as_dict())
         xn = x.double().cpu().numpy()
         gap = (oracle.objective(prob, xn) - fstar) / fstar
