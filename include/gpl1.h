@@ -88,7 +88,26 @@ typedef struct {
                           has, so the solve must end with GPL1_ERR_TIMEOUT after
                           timeout_ns: a fault-free test of the bounded-wait path.      */
   long long timeout_ns; /* bound on every device-side wait                             */
+  int engine;          /* which kernel runs a single solve (gpl1_solve, gpl1_solve_async):
+                          GPL1_ENGINE_AUTO picks the one-read kernel when the instance
+                          fits it (p up to 16 slices of 2048 F32 / 4096 BF16 / 1024 F64
+                          columns, or twice that in two chunks per thread) and the
+                          two-pass kernel otherwise; the batched calls and
+                          gpl1_solve_noalloc always run the two-pass kernel          */
+  int engine_pad;      /* 0                                                             */
 } gpl1_params;
+
+/* gpl1_params.engine.
+ *  ONE_READ: one persistent launch of thread-block clusters that reads K once
+ *    per iteration.  The gradient is linear in the iterate, so the pass that
+ *    forms K x_k and K d_k also forms 2 K^T (K x_k - y) and 2 K^T K d_k from
+ *    the same tiles, and g_{k+1} is their combination with the Armijo step
+ *    (Alg. GP, Steps 5-6).  GPL1_ERR_UNSUPPORTED when the instance does not fit.
+ *  TWO_PASS: one persistent cooperative launch that reads K twice per
+ *    iteration (K^T r, then [K d, K x]). */
+#define GPL1_ENGINE_AUTO 0
+#define GPL1_ENGINE_ONE_READ 1
+#define GPL1_ENGINE_TWO_PASS 2
 
 typedef struct {
   int status;          /* gpl1_status of this instance                                 */

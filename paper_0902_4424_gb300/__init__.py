@@ -24,6 +24,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NOT_CONVERGED", 4: "LINESEAR
 STOP = {0: "rel_gap", 1: "stationary", 2: "fw", 3: "max_iter", 4: "error"}
 STOP_ON_REL_GAP, STOP_ON_FW = 1, 2
 DEBUG_UNREACHABLE_BARRIER = 1
+ENGINE_AUTO, ENGINE_ONE_READ, ENGINE_TWO_PASS = 0, 1, 2
 TRACE_COLS = 28
 # statuses that describe how a solve ended (reported in Result.status, not raised)
 ALGORITHMIC = (0, 3, 4, 5, 6)
@@ -47,7 +48,7 @@ class Params(ctypes.Structure):
                 ("M_alpha", ctypes.c_int), ("tol", ctypes.c_double), ("f_star", ctypes.c_double),
                 ("stop_rule", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_backtracks", ctypes.c_int),
                 ("alpha0_rule", ctypes.c_int), ("x0_is_zero", ctypes.c_int), ("debug", ctypes.c_int),
-                ("timeout_ns", ctypes.c_longlong)]
+                ("timeout_ns", ctypes.c_longlong), ("engine", ctypes.c_int), ("engine_pad", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):

@@ -12,6 +12,7 @@
 #include <numeric>
 #include <vector>
 
+#include "fused.cuh"
 #include "launch.h"
 
 using namespace gpl1;
@@ -30,6 +31,8 @@ struct gpl1_ctx {
   cudaEvent_t ev[2] = {nullptr, nullptr};   // around the solver launch
   // autotuned tensor-core products: (M, N, Kd, Ka, max_splits) -> configuration and split
   std::map<std::vector<long long>, gpl1::GemmChoice> gemm_tuned;
+  // one-read kernel: resident clusters per (dtype, chunks per thread, cluster size)
+  std::map<std::vector<int>, int> fused_resident;
 };
 
 namespace {
@@ -97,10 +100,12 @@ gpl1_status check_params(gpl1_ctx* ctx, const gpl1_params* p) {
   if (p->max_iter < 1 || p->max_backtracks < 0) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad max_iter/max_backtracks");
   if (p->timeout_ns <= 0) return fail(ctx, GPL1_ERR_INVALID_ARG, "timeout_ns must be > 0");
   if (p->alpha0_rule != 0 && p->alpha0_rule != 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "alpha0_rule is 0 or 1");
+  if (p->engine < GPL1_ENGINE_AUTO || p->engine > GPL1_ENGINE_TWO_PASS)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "engine must be GPL1_ENGINE_AUTO, _ONE_READ or _TWO_PASS");
   return GPL1_OK;
 }
 
-gpl1_status check_problem(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, int idx) {
+gpl1_status check_problem(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, int idx, bool two_pass = true) {
   if (!pr) return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d is NULL", idx);
   if (!pr->K || !pr->y || !pr->x) return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d: NULL K, y or x", idx);
   if (pr->n < 1 || pr->p < 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d: n and p must be >= 1", idx);
@@ -115,7 +120,7 @@ gpl1_status check_problem(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, int idx
   const int vs = dt == GPL1_F64 ? 8 : 4;
   if (reinterpret_cast<uintptr_t>(pr->y) % vs || reinterpret_cast<uintptr_t>(pr->x) % vs)
     return fail(ctx, GPL1_ERR_INVALID_ARG, "problem %d: x and y must be aligned to their element size", idx);
-  if (pr->p > static_cast<long long>(gpss_vmax(dt)) * kConsumers)
+  if (two_pass && pr->p > static_cast<long long>(gpss_vmax(dt)) * kConsumers)
     return fail(ctx, GPL1_ERR_UNSUPPORTED, "problem %d: p = %lld exceeds %d for this dtype", idx, pr->p,
                 gpss_vmax(dt) * kConsumers);
   if (pr->n > (1LL << 30) || pr->ldk > (1LL << 31))
@@ -123,7 +128,7 @@ gpl1_status check_problem(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, int idx
   return GPL1_OK;
 }
 
-gpl1_status encode_tmap(gpl1_ctx* ctx, CUtensorMap* map, const gpl1_problem* pr, int dt) {
+gpl1_status encode_tmap(gpl1_ctx* ctx, CUtensorMap* map, const gpl1_problem* pr, int dt, int box_rows = 0) {
   if (!ctx->encode) {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
@@ -138,7 +143,8 @@ gpl1_status encode_tmap(gpl1_ctx* ctx, CUtensorMap* map, const gpl1_problem* pr,
                                                  : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(pr->p), static_cast<cuuint64_t>(pr->n)};
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(pr->ldk) * elem_size(dt)};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kBoxCols), static_cast<cuuint32_t>(rows_per_box(dt))};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kBoxCols),
+                             static_cast<cuuint32_t>(box_rows > 0 ? box_rows : rows_per_box(dt))};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = ctx->encode(map, t, 2, const_cast<void*>(pr->K), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -463,6 +469,155 @@ gpl1_status run(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, con
   return finish_batch(ctx, count, ctx->host_res, res, ctx->ev[0], ctx->ev[1]);
 }
 
+// ---------------------------------------------------------------------------
+// The one-read engine (fused.cuh): shape choice, workspace, launch.
+
+struct OneRead {
+  int nch = 1, C = 1, NC = 0, R = 1, W = 0;
+  long long pp = 0;
+  size_t off_res = 256, off_U = 512, off_parts = 0, total = 0;
+};
+
+// Chunks per thread and cluster size for p columns (the smallest cluster that
+// covers p with one chunk per thread, else with two; portable sizes first),
+// and the number of clusters that stay resident together.
+gpl1_status one_read_choose(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, OneRead* o) {
+  const long long p = pr->p;
+  int nch = 0, C = 0;
+  for (int cand : {1, 2}) {
+    const long long w = fused_width(dt, cand);
+    const long long c = (p + w - 1) / w;
+    if (c <= 8) {
+      nch = cand;
+      C = static_cast<int>(c);
+      break;
+    }
+  }
+  if (!nch) {
+    const long long w = fused_width(dt, 2);
+    const long long c = (p + w - 1) / w;
+    if (c > fz::kCMax)
+      return fail(ctx, GPL1_ERR_UNSUPPORTED, "p = %lld exceeds the one-read kernel's %lld columns", p,
+                  static_cast<long long>(fz::kCMax) * w);
+    nch = 2;
+    C = static_cast<int>(c);
+  }
+  const std::vector<int> key = {dt, nch, C};
+  auto it = ctx->fused_resident.find(key);
+  int resident = 0;
+  if (it == ctx->fused_resident.end()) {
+    cudaError_t e = fused_max_clusters(dt, nch, C, &resident);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      resident = 0;
+    }
+    ctx->fused_resident[key] = resident;
+  } else {
+    resident = it->second;
+  }
+  if (resident < 1)
+    return fail(ctx, GPL1_ERR_UNSUPPORTED, "clusters of %d CTAs of the one-read kernel do not fit this GPU", C);
+  o->nch = nch;
+  o->C = C;
+  o->R = fused_rows(dt, nch);
+  o->W = fused_width(dt, nch);
+  const long long nbt = (pr->n + o->R - 1) / o->R;
+  o->NC = static_cast<int>(std::min<long long>(resident, nbt));
+  o->pp = static_cast<long long>(C) * o->W;
+  const size_t as = static_cast<size_t>(acc_size(dt));
+  o->off_parts = align_up(o->off_U + 3 * 2 * static_cast<size_t>(o->pp) * as, 256);
+  o->total = align_up(o->off_parts + 2 * static_cast<size_t>(o->NC) * C * fz::kPartW * 4, 256);
+  return GPL1_OK;
+}
+
+// Everything one single solve puts on `stream` with the one-read kernel:
+// clear the workspace, launch, copy the result to `res_dst` (kind).
+gpl1_status one_read_enqueue(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl1_params* prm,
+                             const OneRead& o, uint8_t* ws, cudaStream_t stream, void* res_dst, cudaMemcpyKind kind,
+                             cudaEvent_t ev0, cudaEvent_t ev1) {
+  CUtensorMap tmap;
+  std::memset(&tmap, 0, sizeof tmap);
+  gpl1_status st = encode_tmap(ctx, &tmap, pr, dt, o.R);
+  if (st) return st;
+  fz::FArgs fa;
+  std::memset(&fa, 0, sizeof fa);
+  fa.y = pr->y;
+  fa.x = pr->x;
+  fa.rho = pr->rho;
+  fa.f_star = pr->f_star >= 0 ? pr->f_star : prm->f_star;
+  fa.n = static_cast<int>(pr->n);
+  fa.p = static_cast<int>(pr->p);
+  fa.x0_zero = prm->x0_is_zero ? 1 : 0;
+  fa.C = o.C;
+  fa.NC = o.NC;
+  fa.U = ws + o.off_U;
+  fa.pp = o.pp;
+  fa.parts = reinterpret_cast<unsigned*>(ws + o.off_parts);
+  fa.bar = reinterpret_cast<unsigned*>(ws + 64);
+  fa.err = reinterpret_cast<int*>(ws + 128);
+  fa.res = reinterpret_cast<gpl1_result*>(ws + o.off_res);
+  fa.trace = pr->trace;
+  fa.trace_cap = pr->trace ? pr->trace_cap : 0;
+  fa.prm = to_kernel_params(prm);
+  GPL1_CUDA(cudaMemsetAsync(ws, 0, o.total, stream), "cudaMemsetAsync");
+  gpl1_result init;
+  std::memset(&init, 0, sizeof init);
+  init.status = GPL1_ERR_TIMEOUT;   // overwritten by the kernel
+  init.stop = GPL1_STOP_ERROR;
+  GPL1_CUDA(cudaMemcpyAsync(ws + o.off_res, &init, sizeof init, cudaMemcpyHostToDevice, stream),
+            "cudaMemcpyAsync(result)");
+  if (ev0) GPL1_CUDA(cudaEventRecord(ev0, stream), "cudaEventRecord");
+  // a cluster launch of at most the clusters the occupancy query reports
+  // resident together (the kernel's grid barrier waits for all of them, with
+  // a bound)
+  const cudaError_t e = launch_fused(dt, o.nch, &fa, tmap, o.NC, o.C, false, stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "one-read solver launch");
+  if (ev1) GPL1_CUDA(cudaEventRecord(ev1, stream), "cudaEventRecord");
+  GPL1_CUDA(cudaMemcpyAsync(res_dst, ws + o.off_res, sizeof(gpl1_result), kind, stream), "cudaMemcpyAsync(result)");
+  return GPL1_OK;
+}
+
+// Which engine runs this single solve (GPL1_OK with *use_one_read set, or an
+// error for GPL1_ENGINE_ONE_READ on an instance it cannot take).
+gpl1_status pick_engine(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl1_params* prm, OneRead* o,
+                        bool* use_one_read) {
+  *use_one_read = false;
+  if (prm->engine == GPL1_ENGINE_TWO_PASS) return check_problem(ctx, pr, dt, 0, true);
+  gpl1_status st = check_problem(ctx, pr, dt, 0, false);
+  if (st) return st;
+  if (pr->n > (1LL << 30) || pr->p > (1LL << 30)) return fail(ctx, GPL1_ERR_UNSUPPORTED, "n or p too large");
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  st = one_read_choose(ctx, pr, dt, o);
+  if (st == GPL1_OK) {
+    *use_one_read = true;
+    return GPL1_OK;
+  }
+  if (prm->engine == GPL1_ENGINE_ONE_READ) return st;
+  return check_problem(ctx, pr, dt, 0, true);   // the two-pass kernel's own limits
+}
+
+gpl1_status run_one_read(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl1_params* prm, const OneRead& o,
+                         gpl1_result* res, gpl1_result* res_dev) {
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  gpl1_status st = ensure_ws(ctx, o.total);
+  if (st) return st;
+  if (!ctx->ev[0]) {
+    GPL1_CUDA(cudaEventCreate(&ctx->ev[0]), "cudaEventCreate");
+    GPL1_CUDA(cudaEventCreate(&ctx->ev[1]), "cudaEventCreate");
+  }
+  uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
+  if (res_dev)
+    return one_read_enqueue(ctx, pr, dt, prm, o, ws, ctx->stream, res_dev, cudaMemcpyDeviceToDevice, nullptr,
+                            nullptr);
+  st = ensure_host_res(ctx, 1);
+  if (st) return st;
+  st = one_read_enqueue(ctx, pr, dt, prm, o, ws, ctx->stream, ctx->host_res, cudaMemcpyDeviceToHost, ctx->ev[0],
+                        ctx->ev[1]);
+  if (st) return st;
+  GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "solver");
+  return finish_batch(ctx, 1, ctx->host_res, res, ctx->ev[0], ctx->ev[1]);
+}
+
 }  // namespace
 
 gpl1_status gpl1_solve(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype dt, const gpl1_params* prm,
@@ -472,8 +627,11 @@ gpl1_status gpl1_solve(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype dt, c
   if (!res) return fail(ctx, GPL1_ERR_INVALID_ARG, "result is NULL");
   gpl1_status st = check_params(ctx, prm);
   if (st) return st;
-  st = check_problem(ctx, prob, dt, 0);
+  OneRead o;
+  bool one = false;
+  st = pick_engine(ctx, prob, dt, prm, &o, &one);
   if (st) return st;
+  if (one) return run_one_read(ctx, prob, dt, prm, o, res, nullptr);
   return run(ctx, prob, 1, dt, prm, res);
 }
 
@@ -484,8 +642,11 @@ gpl1_status gpl1_solve_async(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype
   if (!res_dev) return fail(ctx, GPL1_ERR_INVALID_ARG, "result is NULL");
   gpl1_status st = check_params(ctx, prm);
   if (st) return st;
-  st = check_problem(ctx, prob, dt, 0);
+  OneRead o;
+  bool one = false;
+  st = pick_engine(ctx, prob, dt, prm, &o, &one);
   if (st) return st;
+  if (one) return run_one_read(ctx, prob, dt, prm, o, nullptr, res_dev);
   return run_async(ctx, prob, 1, dt, prm, res_dev);
 }
 

@@ -52,6 +52,16 @@ int autotune_gemm(PFN_cuTensorMapEncodeTiled_v12000 enc, const void* A, int M, i
                   int N, int Kd, long long ldb, float* out, long long ldo, float scale, int* err, long long timeout_ns,
                   int max_splits, long long split_stride, double sum_gbs, cudaStream_t stream, GemmChoice* best);
 
+// One-read kernel (fused.cu): columns per CTA (W) and rows per block (R) of a
+// configuration, its dynamic shared memory, the number of clusters of C CTAs
+// that stay resident together, and the launch (args: a fz::FArgs).
+int fused_rows(int dt, int nch);
+int fused_width(int dt, int nch);
+size_t fused_smem(int dt, int nch);
+cudaError_t fused_max_clusters(int dt, int nch, int C, int* out);
+cudaError_t launch_fused(int dt, int nch, const void* args, const CUtensorMap& tmap, int clusters, int C,
+                         bool cooperative, cudaStream_t stream);
+
 }  // namespace gpl1
 
 namespace gpl1 {

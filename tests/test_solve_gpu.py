@@ -50,12 +50,17 @@ def small(n, p, k, dtype, seed, law="gauss", rho_scale=0.8, sigma=0.01):
     return W.gaussian(n, p, k, dtype=dtype, seed=seed, law=law, sigma=sigma, rho_scale=rho_scale)
 
 
+ENGINES = [pytest.param(pkg.ENGINE_ONE_READ, id="one_read"), pytest.param(pkg.ENGINE_TWO_PASS, id="two_pass")]
+
+
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("dtype,n,p", [(W.DT_F32, 300, 1000), (W.DT_F32, 97, 301), (W.DT_F64, 256, 1024),
                                        (W.DT_BF16, 300, 1200), (W.DT_F32, 1000, 5000), (W.DT_BF16, 61, 257)])
-def test_small_vs_oracle(gpu_ctx, dtype, n, p):
+def test_small_vs_oracle(gpu_ctx, dtype, n, p, engine):
     prob = small(n, p, max(3, n // 20), dtype, seed=n * 7 + p)
     xs, rs, _ = oracle.reference_solve(prob)
-    x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000)
+    x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000,
+                       engine=engine)
     assert res.status == 0, res.as_dict()
     gap = rel_gap(prob, x, rs.f)
     assert gap <= 1e-6, gap
@@ -78,11 +83,12 @@ def test_config0_fp64_parity(gpu_ctx):
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-6
 
 
-def test_config0_trace_matches_oracle_early(gpu_ctx):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_config0_trace_matches_oracle_early(gpu_ctx, engine):
     """FP64: the first iterations take the same steps as the oracle (same alpha, lambda)."""
     prob = W.config0()
     for iters in (1, 2, 5, 10):
-        x, res = gpu_solve(gpu_ctx, prob, stop_rule=0, max_iter=iters)
+        x, res = gpu_solve(gpu_ctx, prob, stop_rule=0, max_iter=iters, engine=engine)
         xo, ro, tr = oracle.gpss(prob, trace=True, tol=0.0, max_iter=iters)
         assert res.iters == iters and res.status == 3
         np.testing.assert_allclose(x, xo, rtol=0, atol=1e-10 * np.abs(xo).max())
@@ -193,18 +199,46 @@ def test_bounded_wait_reports_timeout(gpu_ctx):
 
 @pytest.mark.parametrize("dtype,p", [(W.DT_F32, 16800), (W.DT_F64, 3840), (W.DT_BF16, 16800)])
 def test_largest_p_the_kernel_stages(gpu_ctx, dtype, p):
-    """p at the limit of the staged x/v vector in shared memory (35 x 480 float
-    entries, 8 x 480 double entries), with a ragged last box of columns."""
+    """p at the limit of the two-pass kernel's staged x/v vector in shared memory
+    (35 x 480 float entries, 8 x 480 double entries), with a ragged last box of
+    columns: solved by both engines; one column more is refused by the two-pass
+    engine and solved by the one-read engine (default)."""
     prob = small(192, p, 12, dtype, seed=p + dtype, rho_scale=0.8)
     xs, rs, _ = oracle.reference_solve(prob)
-    x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000)
-    assert res.status == 0, res.as_dict()
-    assert rel_gap(prob, x, rs.f) <= 1e-6
-    assert np.abs(x).sum() <= prob.rho * (1 + 1e-6)
-    # one column more than the staging holds is refused, not run
+    for engine in (pkg.ENGINE_TWO_PASS, pkg.ENGINE_AUTO):
+        x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000,
+                           engine=engine)
+        assert res.status == 0, (engine, res.as_dict())
+        assert rel_gap(prob, x, rs.f) <= 1e-6, engine
+        assert np.abs(x).sum() <= prob.rho * (1 + 1e-6), engine
+    # one column more than the two-pass staging holds is refused there, not run
     K, y = to_dev(small(8, p + 1, 1, dtype, seed=1))
     with pytest.raises(pkg.Gpl1Error) as e:
-        gpu_ctx.solve(K, y, 1.0)
+        gpu_ctx.solve(K, y, 1.0, params=pkg.params_default(engine=pkg.ENGINE_TWO_PASS))
+    assert e.value.status == 7
+
+
+# columns the one-read engine takes at most: 16 CTAs per cluster, each with
+# two 16-byte chunks per thread of its 512 consumer threads
+ONE_READ_MAX_P = {W.DT_F32: 16 * 2 * 512 * 4, W.DT_F64: 16 * 2 * 512 * 2, W.DT_BF16: 16 * 2 * 512 * 8}
+
+
+@pytest.mark.parametrize("dtype,p", [(W.DT_F32, 24000), (W.DT_F64, 9000)])
+def test_one_read_engine_beyond_the_two_pass_limit(gpu_ctx, dtype, p):
+    """Past the two-pass limit (two chunks per thread, clusters of 6 and 5
+    CTAs): the one-read engine reaches the oracle's optimum; past its own
+    limit it refuses with GPL1_ERR_UNSUPPORTED."""
+    prob = small(192, p, 16, dtype, seed=p + 7 * dtype, rho_scale=0.8)
+    xs, rs, _ = oracle.reference_solve(prob)
+    x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000,
+                       engine=pkg.ENGINE_ONE_READ)
+    assert res.status == 0, res.as_dict()
+    assert rel_gap(prob, x, rs.f) <= 1e-6
+    assert np.linalg.norm(x - xs) <= 1e-3 * np.linalg.norm(xs)
+    big = ONE_READ_MAX_P[dtype] + 1
+    K, y = to_dev(small(4, big, 1, dtype, seed=2))
+    with pytest.raises(pkg.Gpl1Error) as e:
+        gpu_ctx.solve(K, y, 1.0, params=pkg.params_default(engine=pkg.ENGINE_ONE_READ))
     assert e.value.status == 7
 
 
