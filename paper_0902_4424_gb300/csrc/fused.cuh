@@ -55,7 +55,10 @@ constexpr int kThr = kCons + 96;        // + TMA producer warp, sender warp, tot
 constexpr int kProd = kCons;            // first thread of the producer warp
 constexpr int kSend = kCons + 32;       // ... of the sender warp
 constexpr int kTot = kCons + 64;        // ... of the totaler warp
-constexpr int kNST = 5;                 // stages of the K ring
+constexpr int kNSA = 3;                 // stages of the ring that streams K from HBM (A steps)
+constexpr int kNSB = 2;                 // stages of the ring that re-reads blocks from L2 (B steps)
+constexpr int kNST = kNSA + kNSB;
+constexpr int CTL_ISSUED_B = 7;         // (sm.ctl) loads issued into the B ring
 constexpr int kStageBytes = 32768;      // one row block of one CTA's slice
 constexpr int kBoxW = 256;              // TMA box width (elements)
 constexpr int kCMax = 16;               // CTAs per cluster
@@ -450,7 +453,7 @@ struct FC {
   const unsigned rank, cid;
   const int C, NC, G, cta, n, p;
   int bk0, bk1;
-  uint32_t ita = 0, rseq = 0, sseq = 0;
+  uint32_t ita = 0, itb = 0, rseq = 0, sseq = 0;
   unsigned epoch = 0;
   int bsl = 0;
   int status = GPL1_OK;
@@ -538,9 +541,8 @@ struct FC {
     if (lane == 0) {
       volatile int* ctl = sm.ctl;
       const uint64_t t0 = globaltimer();
-      for (unsigned it = 0;; ++it) {
-        if (cl ? mbar_test_cl(bar, par) : mbar_test(bar, par)) break;
-        if ((it & 63u) != 63u) continue;
+      for (;;) {
+        if (cl ? mbar_wait_h_cl(bar, par) : mbar_wait_h(bar, par)) break;
         if (ctl[CTL_STOP] || failed()) {
           ok = 0;
           break;
@@ -1003,7 +1005,7 @@ struct FC {
   // this CTA's outgoing slot have completed.
   __device__ bool rx_send(uint32_t seq, const uint32_t (&wd)[RWPR]) {
     const uint32_t slot = seq % kRNS, use = seq / kRNS;
-    if (use >= 1 && !wwait(&sm.rempty[slot], (use - 1) & 1u, kSiteRowMsg, true, true)) return false;
+    if (use >= 1 && !wwait(&sm.rempty[slot], (use - 1) & 1u, kSiteRowMsg, true)) return false;
     if (lane % LPR == 0) {
       uint32_t* o = &sm.xout[slot][RWPR * (lane / LPR)];
 #pragma unroll
@@ -1062,52 +1064,44 @@ struct FC {
     const bool dots = !(SETUP && a.x0_zero);
     const V* yg = static_cast<const V*>(a.y);
     const uint32_t rs0 = rseq;
-    uint32_t it = ita;
 #pragma unroll 1
     for (int c = 0; c < ncks + kLagC; ++c) {
-      // ---- step A(c): the row sums of chunk c
-      if (c < ncks) {
-        const int cnt = min(kCB, nb - c * kCB);
-        const uint32_t seq = rs0 + c, s3 = seq % kNRed;
+      const bool hasA = c < ncks, hasB = c >= kLagC;
+      const int cntA = hasA ? min(kCB, nb - c * kCB) : 0;
+      const int cb = c - kLagC;
+      const int cntB = hasB ? min(kCB, nb - cb * kCB) : 0;
+      const uint32_t seq = rs0 + c, s3 = seq % kNRed;
+      const uint32_t m = rs0 + cb, ts = m % kNTot;
+      bool okt = true;
+      // y of the chunk's rows (warp 0, lane = row of the chunk), loaded once
+      // at the start of the chunk and handed to the totaler after its blocks
+      A ych = 0;
+      bool vch = false;
+      if (hasA && dots && warp == 0 && lane < RC) {
+        const int jj = lane / R;
+        const int qb = c * kCB + jj;
+        const int row = (fwd ? bk0 + qb : bk1 - 1 - qb) * R + lane % R;
+        vch = jj < cntA && row < n;
+        if (vch) ych = static_cast<A>(yg[row]);
+      }
 #pragma unroll 1
-        for (int j = 0; j < kCB; ++j) {
-          if (j < cnt) {
-            const int qb = c * kCB + j;
-            const int b = fwd ? bk0 + qb : bk1 - 1 - qb;
-            const int row = b * R + lane;
-            A yv = 0;
-            if (dots && warp == 0 && lane < R && row < n) yv = static_cast<A>(yg[row]);
-            const uint32_t st = it % kNST;
-            const bool ok = wwait(&sm.full[st], (it / kNST) & 1u, kSitePassA, false);
+      for (int j = 0; j < kCB; ++j) {
+        // ---- step A: block j of chunk c (from HBM): its row sums
+        if (hasA) {
+          if (j < cntA) {
+            const uint32_t st = ita % kNSA;
+            const bool ok = wwait(&sm.full[st], (ita / kNSA) & 1u, kSitePassA, false);
             if (dots && ok) row_partials<ACC>(sm.stage[st], &sm.red[s3][warp][RWPR * R * j]);
             __syncwarp();
             if (lane == 0 && ok) mbar_arrive(&sm.empty[st]);
-            ++it;
-            if (dots && warp == 0 && lane < R) {
-              uint32_t* yw = sm.ysm[s3][j * R + lane];
-              put(yw, yv);   // a float occupies the first word, a double the first two
-              yw[2] = row < n ? 1u : 0u;
-            }
+            ++ita;
           } else if (dots) {   // past the last block of the pass
             if (lane < RWPR * R) sm.red[s3][warp][RWPR * R * j + lane] = 0u;
-            if (warp == 0 && lane < R) sm.ysm[s3][j * R + lane][2] = 0u;
           }
         }
-        if (dots) {
-          if (warp == 0 && lane == 0) sm.bmode[s3] = ACC ? 1u : 0u;
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sm.redfull[s3]);
-        }
-      }
-      // ---- step B(c - kLagC): the K^T step of chunk c - kLagC
-      if (c >= kLagC) {
-        const int cb = c - kLagC;
-        const int cnt = min(kCB, nb - cb * kCB);
-        const uint32_t m = rs0 + cb, ts = m % kNTot;
-        bool okt = true;
-        if (dots) okt = wwait(&sm.tfull[ts], (m / kNTot) & 1u, kSiteRowMsg, false, true);
-#pragma unroll 1
-        for (int j = 0; j < cnt; ++j) {
+        // ---- step B: block j of chunk c - kLagC (from L2): its K^T step
+        if (hasB && j < cntB) {
+          if (dots && j == 0) okt = wwait(&sm.tfull[ts], (m / kNTot) & 1u, kSiteRowMsg, false);
           const int qb = cb * kCB + j;
           const int b = fwd ? bk0 + qb : bk1 - 1 - qb;
           A m1[R], m2[R];
@@ -1136,8 +1130,8 @@ struct FC {
               m2[qq] = A(0);
             }
           }
-          const uint32_t st = it % kNST;
-          const bool ok = wwait(&sm.full[st], (it / kNST) & 1u, kSitePassB, false);
+          const uint32_t st = kNSA + itb % kNSB;
+          const bool ok = wwait(&sm.full[st], (itb / kNSB) & 1u, kSitePassB, false);
           if (ok && okt) {
             const uint8_t* stg = sm.stage[st];
 #pragma unroll
@@ -1157,15 +1151,24 @@ struct FC {
           }
           __syncwarp();
           if (lane == 0 && ok) mbar_arrive(&sm.empty[st]);
-          ++it;
-        }
-        if (dots) {
-          __syncwarp();
-          if (lane == 0 && okt) mbar_arrive(&sm.tcons[ts]);
+          ++itb;
         }
       }
+      if (hasA && dots) {
+        if (warp == 0 && lane < RC) {
+          uint32_t* yw = sm.ysm[s3][lane];
+          put(yw, ych);   // a float occupies the first word, a double the first two
+          yw[2] = vch ? 1u : 0u;
+        }
+        if (warp == 0 && lane == 0) sm.bmode[s3] = ACC ? 1u : 0u;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.redfull[s3]);
+      }
+      if (hasB && dots) {
+        __syncwarp();
+        if (lane == 0 && okt) mbar_arrive(&sm.tcons[ts]);
+      }
     }
-    ita = it;
     if (dots) {
       rseq = rs0 + ncks;
       // the row scalars the totaler added (cluster rank 0); cleared for the
@@ -1335,7 +1338,7 @@ struct FC {
         y = 0;
       }
       const uint32_t ts = m % kNTot;
-      if (m >= kNTot && !wwait(&sm.tcons[ts], ((m - kNTot) / kNTot) & 1u, kSiteRowMsg, false, true)) break;
+      if (m >= kNTot && !wwait(&sm.tcons[ts], ((m - kNTot) / kNTot) & 1u, kSiteRowMsg, false)) break;
       if (g == 0) {
         const A m1 = A(2) * lead(r), m2 = A(2) * kd;
         if constexpr (!kF64) {
@@ -1798,16 +1801,19 @@ struct FC {
       }
     }
     __threadfence_block();
-    const uint32_t issued = static_cast<uint32_t>(ctl[CTL_ISSUED]);
     if (tid == 0) {
-      // the last copy issued into every stage (earlier ones completed their
-      // phases before it could be issued)
-      for (uint32_t s = 0; s < kNST && s < issued; ++s) {
-        const uint32_t last = issued - 1 - ((issued - 1 - s) % kNST);
-        const uint32_t par = (last / kNST) & 1u;
-        const uint64_t t1 = globaltimer();
-        while (!mbar_try_wait(&sm.full[s], par))
-          if (globaltimer() - t1 > kInflightNs) break;
+      // the last copy issued into every stage of both rings (earlier ones
+      // completed their phases before it could be issued)
+      for (int ring = 0; ring < 2; ++ring) {
+        const uint32_t issued = static_cast<uint32_t>(ctl[ring ? CTL_ISSUED_B : CTL_ISSUED]);
+        const uint32_t ns = ring ? kNSB : kNSA, base = ring ? kNSA : 0;
+        for (uint32_t s = 0; s < ns && s < issued; ++s) {
+          const uint32_t last = issued - 1 - ((issued - 1 - s) % ns);
+          const uint32_t par = (last / ns) & 1u;
+          const uint64_t t1 = globaltimer();
+          while (!mbar_try_wait(&sm.full[base + s], par))
+            if (globaltimer() - t1 > kInflightNs) break;
+        }
       }
     }
     csync();
@@ -1933,47 +1939,56 @@ __device__ void producer(const FArgs& a, const CUtensorMap* tmap, FSmem<DT, NCH>
   const int rest = a.p - c0;
   const int nbox = rest <= 0 ? 0 : min(CF::NBOX, (rest + kBoxW - 1) / kBoxW);
   volatile int* ctl = sm.ctl;
-  uint32_t it = 0;
-  const int ncks = (nb + kCB - 1) / kCB;
-  // one row block into the next stage of the ring; false when stopped
-  auto issue = [&](int b) -> bool {
-    const uint32_t st = it % kNST;
-    const uint32_t par = ((it / kNST) & 1u) ^ 1u;
-    uint64_t t0 = 0;
-    while (!mbar_try_wait(&sm.empty[st], par)) {
-      if (ctl[CTL_STOP]) return false;
-      const uint64_t t = globaltimer();
-      if (t0 == 0) t0 = t;
-      else if (t - t0 > static_cast<uint64_t>(a.prm.timeout_ns)) {
-        if (!ctl[CTL_ERR]) ctl[CTL_SITE] = kSiteProducer;
-        ctl[CTL_ERR] = GPL1_ERR_TIMEOUT;
-        return false;
-      }
-    }
-    if (ctl[CTL_STOP]) return false;
+  // Two streams of the same block sequence (pass after pass, serpentine):
+  // A into the A ring (the first read of a block, from HBM), B into the B
+  // ring (the second read, normally served by L2).  A block's B load is issued
+  // only after its A load.  The lane polls both rings' empty barriers and
+  // issues into whichever has room.
+  uint32_t ia = 0, ib = 0;   // loads issued per ring
+  int pa = 0, qa = 0, pb = 0, qb = 0;   // (pass, position in the pass) of the next A and B block
+  auto block_of = [&](int pass, int q) { return (pass & 1) == 0 ? bk0 + q : bk1 - 1 - q; };
+  auto load = [&](int st, int b) {
     mbar_arrive_expect_tx(&sm.full[st], static_cast<uint32_t>(nbox * CF::BOXB));
     for (int i = 0; i < nbox; ++i)
       tma_load_2d(sm.stage[st] + i * CF::BOXB, tmap, &sm.full[st], c0 + i * kBoxW, b * R);
-    ++it;
-    ctl[CTL_ISSUED] = static_cast<int>(it);
-    return true;
   };
   if (nb > 0) {
-    // the consumers' order: the blocks of chunk c, then again those of chunk
-    // c - kLagC, pass after pass (serpentine)
-    for (int s = 0;; ++s) {
-      const bool fwd = (s & 1) == 0;
-      for (int c = 0; c < ncks + kLagC; ++c) {
-        if (c < ncks)
-          for (int j = 0; j < kCB && c * kCB + j < nb; ++j) {
-            const int qb = c * kCB + j;
-            if (!issue(fwd ? bk0 + qb : bk1 - 1 - qb)) goto done;
-          }
-        if (c >= kLagC)
-          for (int j = 0; j < kCB && (c - kLagC) * kCB + j < nb; ++j) {
-            const int qb = (c - kLagC) * kCB + j;
-            if (!issue(fwd ? bk0 + qb : bk1 - 1 - qb)) goto done;
-          }
+    uint64_t t0 = globaltimer();
+    for (unsigned poll = 0;; ++poll) {
+      bool did = false;
+      if (mbar_test(&sm.empty[ia % kNSA], ((ia / kNSA) & 1u) ^ 1u)) {
+        if (ctl[CTL_STOP]) goto done;
+        load(static_cast<int>(ia % kNSA), block_of(pa, qa));
+        ++ia;
+        ctl[CTL_ISSUED] = static_cast<int>(ia);
+        if (++qa == nb) {
+          qa = 0;
+          ++pa;
+        }
+        did = true;
+      }
+      if (ib < ia && mbar_test(&sm.empty[kNSA + ib % kNSB], ((ib / kNSB) & 1u) ^ 1u)) {
+        if (ctl[CTL_STOP]) goto done;
+        load(static_cast<int>(kNSA + ib % kNSB), block_of(pb, qb));
+        ++ib;
+        ctl[CTL_ISSUED_B] = static_cast<int>(ib);
+        if (++qb == nb) {
+          qb = 0;
+          ++pb;
+        }
+        did = true;
+      }
+      if (did) {
+        t0 = globaltimer();
+        continue;
+      }
+      __nanosleep(128);   // nothing to issue: yield the issue slots to the consumer warps
+      if ((poll & 15u) != 15u) continue;
+      if (ctl[CTL_STOP]) goto done;
+      if (globaltimer() - t0 > static_cast<uint64_t>(a.prm.timeout_ns)) {
+        if (!ctl[CTL_ERR]) ctl[CTL_SITE] = kSiteProducer;
+        ctl[CTL_ERR] = GPL1_ERR_TIMEOUT;
+        goto done;
       }
     }
   }
