@@ -12,10 +12,13 @@ optimum stored in tests/golden/fstar.json.
 Prints one JSON line (rank 0).  `value` is device-timed with inputs resident in
 HBM; `e2e` repeats the measurement through the public API with the inputs in
 pinned host memory (host-to-device copy of K and y and the device-to-host read
-of x inside every step).  `roofline` compares the solver kernel's algorithmic
-HBM bytes (two reads of K per iteration) per launch with its event-timed
-duration.  `cpu_baseline` times the FP64 oracle on this host's cores on one
-solve of the same workload.  `--impl reference` runs only that oracle arm.
+of x inside every step).  The solve runs on the library's default engine, the
+one-read kernel, whose algorithmic HBM traffic is one read of K per pass (one
+pass per iteration plus the setup pass that forms g_0); `roofline` compares
+those bytes per launch with the kernel's event-timed duration.  `two_pass`
+times the same solves on the two-pass kernel (two reads of K per iteration).
+`cpu_baseline` times the FP64 oracle on this host's cores on whole solves of
+the same workload.  `--impl reference` runs only that oracle arm.
 """
 from __future__ import annotations
 
@@ -559,7 +562,8 @@ def run_ours(args, rank, world, local_rank):
     y = y_host.to(dev)
     x = torch.zeros(p, dtype=torch.float32, device=dev)
     ctx = pkg.Context(local_rank)
-    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=TOL, f_star=fstar, x0_is_zero=1, max_iter=20000)
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=TOL, f_star=fstar, x0_is_zero=1, max_iter=20000,
+                             engine=pkg.ENGINE_ONE_READ)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MiB > L2
 
     def solve():
@@ -641,15 +645,16 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    # ---- roofline of the solver kernel: 2 reads of K per iteration
-    bytes_per_iter = 2.0 * n * p * prob.K.itemsize
+    # ---- roofline of the solver kernel: one read of K per pass, one pass per
+    # iteration plus the setup pass
+    bytes_per_pass = 1.0 * n * p * prob.K.itemsize
     mean_iters = statistics.mean(iters)
-    algo_bytes = bytes_per_iter * mean_iters
+    algo_bytes = bytes_per_pass * (mean_iters + 1)
     kms = statistics.mean(kernel_ms)
     achieved = algo_bytes / (kms / 1e3) / 1e9
     peak, peak_kind = peaks()
     traffic = None
-    tr_file = os.path.join(ROOT, "profiles", "gpss_kernel_c1_f32_traffic.txt")   # JSON text
+    tr_file = os.path.join(ROOT, "profiles", "fused_kernel_c1_f32_traffic.txt")   # JSON text
     if os.path.exists(tr_file):
         with open(tr_file) as fh:
             tr = json.load(fh)
@@ -679,12 +684,20 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "frac_of_nominal_8tbs": achieved / 8000.0,
-                     "algorithmic_bytes_per_launch": algo_bytes, "kernel_ms": kms},
+                     "kernel": "gpl1::fz::fused_kernel<1,1> (one-read engine)",
+                     "algorithmic_bytes_per_launch": algo_bytes,
+                     "algorithmic_bytes": "one read of K (n p 4 B) per pass; passes = iterations + 1",
+                     "kernel_ms": kms},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
+    if args.extras:
+        line["two_pass"] = run_engine_compare(ctx, K, y, prob, prm, flush, args.steps, dev)
+        line["fw_stop"] = run_fw_stop(ctx, K, y, prob, fstar, flush, args.steps, dev)
+        line["c0"] = run_small_config("c0", dev, 20)
+        line["c2"] = run_small_config("c2", dev, 10)
     if args.batched_sample > 0:
         line["batched"] = run_batched(args.batched_sample, 3, dev)
     if args.shared_k > 0 and os.path.exists(os.path.join(ROOT, "tests", "golden", "c3b_fstar.json")):
@@ -697,13 +710,119 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
 
+def timed_solves(ctx, K, y, prob, prm, flush, steps, dev):
+    """Device time (ms per solve) and results of `steps` solves, L2 flushed before each."""
+    import torch
+    stream = torch.cuda.current_stream()
+    x = torch.zeros(prob.p, dtype=torch.float64 if K.dtype == torch.float64 else torch.float32, device=dev)
+    ms, res = [], []
+    for s in range(steps):
+        flush.fill_(float(s))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, r = ctx.solve(K, y, prob.rho, x=x, p=prob.p, params=prm)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        res.append(r)
+    return ms, res
+
+
+def run_engine_compare(ctx, K, y, prob, prm, flush, steps, dev):
+    """The same solves (c1, stop at the 1e-6 gap) on the two-pass kernel, which
+    reads K twice per iteration (K^T r, then [K d, K x]); its roofline counts
+    those two reads."""
+    import paper_0902_4424_gb300 as pkg
+    prm2 = pkg.Params.from_buffer_copy(prm)
+    prm2.engine = pkg.ENGINE_TWO_PASS
+    timed_solves(ctx, K, y, prob, prm2, flush, 2, dev)
+    ms, res = timed_solves(ctx, K, y, prob, prm2, flush, steps, dev)
+    iters = statistics.mean(r.iters for r in res)
+    kms = statistics.mean(r.kernel_ms for r in res)
+    algo = 2.0 * prob.n * prob.p * prob.K.itemsize * iters
+    peak, _ = peaks()
+    return {"kernel": "gpl1::gpss_kernel<1> (two-pass engine)", "solves_per_s": 1e3 / statistics.mean(ms),
+            "ms_per_solve": statistics.mean(ms), "iters_per_solve": iters, "kernel_ms": kms,
+            "hbm_gbs": algo / (kms / 1e3) / 1e9, "roofline_frac": algo / (kms / 1e3) / 1e9 / peak,
+            "algorithmic_bytes": "two reads of K per iteration", "ok": sum(r.status == 0 for r in res)}
+
+
+def run_fw_stop(ctx, K, y, prob, fstar, flush, steps, dev):
+    """Time to tolerance as a user without f* gets it: the stop on the Frank-Wolfe
+    certificate g^T x + rho ||g||_inf <= tol (f - cert) (an upper bound of the
+    relative gap), at the tolerances an FP32 gradient can certify on this
+    instance (the certificate cancels two terms of size rho ||g||_inf, about 70 f
+    here, so FP32 rounding of g bounds what it resolves near 1e-6); the returned
+    x's gap checked in FP64."""
+    import torch
+
+    import paper_0902_4424_gb300 as pkg
+    out = {"stop": "FW certificate <= tol (f - cert), no f*"}
+    for tol in (1e-4, 1e-5):
+        prm = pkg.params_default(stop_rule=pkg.STOP_ON_FW, tol=tol, x0_is_zero=1, max_iter=2000,
+                                 engine=pkg.ENGINE_ONE_READ)   # x0 = 0 (x0_is_zero) in every solve
+        timed_solves(ctx, K, y, prob, prm, flush, 1, dev)
+        ms, res = timed_solves(ctx, K, y, prob, prm, flush, min(steps, 10), dev)
+        x, r = ctx.solve(K, y, prob.rho, p=prob.p, params=prm)
+        torch.cuda.synchronize()
+        gap = (objective_f64(prob, x.double().cpu().numpy()) - fstar) / fstar
+        out[f"tol_{tol:g}"] = {"solves_per_s": 1e3 / statistics.mean(ms), "ms_per_solve": statistics.mean(ms),
+                               "iters_per_solve": statistics.mean(r.iters for r in res),
+                               "stop_reasons": sorted({pkg.STOP[r.stop] for r in res}),
+                               "verified_rel_gap": gap, "ok": sum(r.status == 0 for r in res)}
+    return out
+
+
+def run_small_config(name, dev, steps):
+    """c0 (FP64 256 x 1024: K is 2 MiB, L2-resident, so latency- and barrier-bound:
+    microseconds per iteration) and c2 (FP32 4096 x 4096 ill-conditioned: 64 MiB,
+    inside L2 between passes, reported as effective GB/s), each on both engines to
+    the 1e-6 gap against the stored oracle optimum; c0 also times the oracle
+    single-threaded (whole solves)."""
+    import torch
+
+    import oracle
+    import paper_0902_4424_gb300 as pkg
+    import workloads as W
+    prob = {"c0": W.config0, "c2": W.config2}[name]()
+    fstar = golden(name)["f_star"]
+    K = torch.from_numpy(prob.K).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    ctx = pkg.Context(dev.index or 0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"workload": prob.name, "n": prob.n, "p": prob.p}
+    for label, engine, reads in (("one_read", pkg.ENGINE_ONE_READ, None), ("two_pass", pkg.ENGINE_TWO_PASS, 2.0)):
+        prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=TOL, f_star=fstar, x0_is_zero=1,
+                                 max_iter=20000, engine=engine)
+        timed_solves(ctx, K, y, prob, prm, flush, 2, dev)
+        ms, res = timed_solves(ctx, K, y, prob, prm, flush, steps, dev)
+        iters = statistics.mean(r.iters for r in res)
+        kms = statistics.mean(r.kernel_ms for r in res)
+        byts = (iters + 1 if reads is None else reads * iters) * prob.n * prob.p * prob.K.itemsize
+        out[label] = {"solves_per_s": 1e3 / statistics.mean(ms), "iters_per_solve": iters,
+                      "us_per_iter": 1e3 * kms / max(iters, 1), "effective_gbs": byts / (kms / 1e3) / 1e9,
+                      "ok": sum(r.status == 0 for r in res)}
+    if name == "c0":
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        _, r, _ = oracle.gpss(prob, f_star=fstar, tol=TOL)
+        dt = time.perf_counter() - t0
+        oracle.set_threads(0)
+        out["oracle_1thread"] = {"us_per_iter": 1e6 * dt / max(r.iters, 1), "iters": r.iters, "cores": 1,
+                                 "solves_per_s": 1.0 / dt}
+    if name == "c2":
+        out["note"] = "K (64 MiB) stays in L2 between passes: effective GB/s, not an HBM roofline"
+    ctx.close()
+    return out
+
+
 def kernel_fingerprint():
     """Hash of the sources the solver kernel is compiled from; a stored DRAM-traffic
     figure is only used while it matches."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0902_4424_gb300", "csrc")
-    for name in ("common.cuh", "gpss.cuh", "project.cuh", "gpss_f32.cu"):
+    for name in ("common.cuh", "gpss.cuh", "project.cuh", "fused.cuh", "fused.cu"):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -726,6 +845,8 @@ def main():
                          "K^T R and K D (to reproduce a configuration under a profiler)")
     ap.add_argument("--warm-start", type=int, default=1, help="also measure the learned warm start (0: skip)")
     ap.add_argument("--rho-sweep", type=int, default=1, help="also measure the 50-radius sweep (0: skip)")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="also time c1 on the two-pass engine and with the FW stop, and c0 and c2 (0: skip)")
     ap.add_argument("--workload", choices=["c1", "c3a"], default="c1",
                     help="c3a: only the batched ragged form, all 512 instances")
     args = ap.parse_args()

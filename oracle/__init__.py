@@ -92,6 +92,11 @@ def num_threads() -> int:
     return int(lib().ora_num_threads())
 
 
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on (for a single-threaded timing)."""
+    lib().ora_set_threads(ctypes.c_int(int(n)))
+
+
 def project(v, rho: float):
     """Euclidean projection onto the l1 ball of radius rho; returns (w, tau)."""
     v = np.ascontiguousarray(v, dtype=np.float64)

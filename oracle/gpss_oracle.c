@@ -37,6 +37,10 @@ static double k_at(const void* K, int dtype, long ldk, long i, long j) {
   return (double)f;
 }
 
+void ora_set_threads(int n) {
+  if (n > 0) omp_set_num_threads(n);
+}
+
 int ora_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -83,6 +83,8 @@ void ora_certificates(const void* K, int dtype, long n, long p, long ldk, const 
 
 /* Number of OpenMP threads the oracle uses. */
 int ora_num_threads(void);
+/* Threads of the OpenMP loops (n > 0), e.g. 1 for a single-threaded timing. */
+void ora_set_threads(int n);
 
 #ifdef __cplusplus
 }
