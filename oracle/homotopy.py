@@ -36,14 +36,28 @@ def solve_at_radius(K, y, rho: float, max_segments: int = 10000):
     """x minimising ||K x - y||^2 subject to ||x||_1 <= rho, and lam = max|K^T (y - K x)|.
     Returns (x, lam, segments walked).  If the least-squares path ends before
     ||x||_1 reaches rho (the constraint is inactive), returns the end of the path."""
+    return solve_at_radii(K, y, [rho], max_segments)[0]
+
+
+def solve_at_radii(K, y, radii, max_segments: int = 10000):
+    """solve_at_radius for several radii in one walk down the path: a list of
+    (x, lam, segments walked) in the order of `radii`.  The walk is the same for
+    every radius, so each entry equals the single-radius result."""
     K = np.asarray(K, np.float64)
     y = np.asarray(y, np.float64)
     n, p = K.shape
+    order = np.argsort(np.asarray(radii, np.float64), kind="stable")
+    out = [None] * len(order)
+    pending = [int(i) for i in order]          # radii not reached yet, smallest first
     x = np.zeros(p)
     c = K.T @ y
     lam = float(np.max(np.abs(c)))
-    if lam == 0.0 or rho <= 0.0:
-        return x, lam, 0
+    for i in list(pending):
+        if lam == 0.0 or radii[i] <= 0.0:
+            out[i] = (x.copy(), lam, 0)
+            pending.remove(i)
+    if not pending:
+        return out
     active = [int(np.argmax(np.abs(c)))]
     just_joined, just_left = active[0], -1
     for seg in range(1, max_segments + 1):
@@ -54,28 +68,38 @@ def solve_at_radius(K, y, rho: float, max_segments: int = 10000):
         a = K.T @ (KA @ delta)           # dc/dgamma = -a
         l1 = float(np.sum(np.abs(x)))
         dl1 = float(s @ delta)           # d||x||_1 / dgamma on this segment
-        # candidate events along gamma > 0
-        gamma, event = lam, ("end", -1)  # lam cannot drop below 0
+        # the first event along gamma in (0, lam): an inactive correlation
+        # reaching +-(lam - gamma) (the smallest index, + before -, on ties), else
+        # an active entry reaching 0 strictly earlier
+        gamma, event = lam, ("end", -1)
         inactive = np.setdiff1d(np.arange(p), A)
-        for j in inactive:
-            if j == just_left:
-                continue
-            for sgn in (1.0, -1.0):      # c_j - gamma a_j = sgn (lam - gamma)
-                den = sgn - a[j]
-                if den != 0.0:
-                    g = (sgn * lam - c[j]) / den
-                    if 0.0 < g < gamma:
-                        gamma, event = g, ("join", int(j))
-        for q, j in enumerate(A):
-            if delta[q] != 0.0 and j != just_joined:
-                g = -x[j] / delta[q]
-                if 0.0 < g < gamma:
-                    gamma, event = g, ("leave", int(j))
-        # does ||x||_1 reach rho on this segment?
-        if dl1 > 0.0 and l1 + gamma * dl1 >= rho:
-            g = (rho - l1) / dl1
-            x[A] += g * delta
-            return _checked(K, y, x, lam - g), lam - g, seg
+        if just_left >= 0:
+            inactive = inactive[inactive != just_left]
+        if inactive.size:
+            sg = np.array([1.0, -1.0])
+            den = sg[None, :] - a[inactive][:, None]
+            with np.errstate(divide="ignore", invalid="ignore"):
+                g = (sg[None, :] * lam - c[inactive][:, None]) / den
+            g = np.where((den != 0.0) & (g > 0.0) & (g < gamma), g, np.inf).ravel()
+            q = int(np.argmin(g))
+            if np.isfinite(g[q]):
+                gamma, event = float(g[q]), ("join", int(inactive[q // 2]))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            gl = -x[A] / delta
+        gl = np.where((delta != 0.0) & (A != just_joined) & (gl > 0.0) & (gl < gamma), gl, np.inf)
+        if gl.size:
+            q = int(np.argmin(gl))
+            if np.isfinite(gl[q]):
+                gamma, event = float(gl[q]), ("leave", int(A[q]))
+        # the radii that ||x||_1 reaches on this segment
+        while pending and dl1 > 0.0 and l1 + gamma * dl1 >= radii[pending[0]]:
+            i = pending.pop(0)
+            g = (radii[i] - l1) / dl1
+            xr = x.copy()
+            xr[A] += g * delta
+            out[i] = (_checked(K, y, xr, lam - g), lam - g, seg)
+        if not pending:
+            return out
         x[A] += gamma * delta
         c = c - gamma * a
         lam -= gamma
@@ -87,10 +111,12 @@ def solve_at_radius(K, y, rho: float, max_segments: int = 10000):
             active.remove(event[1])
             x[event[1]] = 0.0
             just_left = event[1]
-        else:   # lam reached 0: the least-squares end of the path
-            return x, 0.0, seg
-        if len(active) > min(n, p):
-            return x, lam, seg
+        if event[0] == "end" or len(active) > min(n, p):
+            # the least-squares end of the path (lam = 0) or a full active set:
+            # the constraint is inactive for the radii left
+            for i in pending:
+                out[i] = (x.copy(), 0.0 if event[0] == "end" else lam, seg)
+            return out
     raise RuntimeError("homotopy did not reach the radius")
 
 

@@ -26,7 +26,11 @@ Backward (one subgradient of S: dS/dz = 1[|z| > t], dS/dt = -sgn(z) 1[|z| > t]):
 Pins (tests/test_oracle_pins.py): one layer on an orthonormal K is the closed-
 form minimiser of eq. 1; many tied ISTA layers reach the optimality conditions
 of eq. 1 (|K^T (y - Kx)| <= lambda, equality with the sign of x on the
-support); the backward pass against central finite differences.
+support); the backward pass against central finite differences.  The BF16
+precision model (rounded=True): the rounding against torch's bfloat16
+conversion; with data whose products need no rounding it equals the FP64
+network; and its distance to the FP64 network stays within the BF16 error
+bound.
 """
 from __future__ import annotations
 
@@ -37,20 +41,44 @@ def soft(z, t):
     return np.sign(z) * np.maximum(np.abs(z) - t, 0.0)
 
 
-def forward(K, W, theta, Y):
+def bf16(a):
+    """Round to the nearest bfloat16 (ties to even), returned as float64: the 16
+    high bits of the float32 pattern after adding half of the dropped part
+    (0x7fff, plus 1 when the kept part is odd).  Finite inputs only."""
+    b = np.ascontiguousarray(np.asarray(a, np.float32)).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _precision(rounded: bool):
+    """(operand rounding of a product, rounding of a stored value): identity in
+    FP64, or BF16 operands and FP32 values (the tensor-core precision model)."""
+    if not rounded:
+        ident = lambda a: np.asarray(a, np.float64)   # noqa: E731
+        return ident, ident
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)   # noqa: E731
+    return bf16, f32
+
+
+def forward(K, W, theta, Y, rounded: bool = False):
     """K (n, p); W (L, p, n); theta (L,); Y (B, n).  Returns (xs, zs): xs[l] (B, p)
-    for l = 0..L (xs[0] = 0) and zs[l] (B, p) the pre-threshold values of layer l."""
+    for l = 0..L (xs[0] = 0) and zs[l] (B, p) the pre-threshold values of layer l.
+
+    rounded=True is the precision model of a tensor-core implementation: the
+    operands of every matrix product rounded to BF16 (products summed exactly
+    here, in FP32 there), every stored result and elementwise step in FP32."""
+    op, st = _precision(rounded)
     K = np.asarray(K, np.float64)
-    Y = np.asarray(Y, np.float64)
+    Y = st(Y)
     L = W.shape[0]
     B, p = Y.shape[0], K.shape[1]
     xs = [np.zeros((B, p))]
     zs = []
     for l in range(L):
-        r = Y - xs[l] @ K.T                 # y - K x^l, per sample
-        z = xs[l] + r @ np.asarray(W[l], np.float64).T
+        r = st(Y - st(op(xs[l]) @ op(K).T))                 # y - K x^l, per sample
+        z = st(xs[l] + st(op(r) @ op(W[l]).T))
         zs.append(z)
-        xs.append(soft(z, theta[l]))
+        xs.append(st(soft(z, st(theta[l]))))
     return xs, zs
 
 
@@ -59,23 +87,25 @@ def loss(xL, Xt):
     return float(np.sum(d * d) / d.shape[0])
 
 
-def backward(K, W, theta, Y, Xt):
-    """Loss and its gradients (dW (L, p, n), dtheta (L,)) for one batch."""
+def backward(K, W, theta, Y, Xt, rounded: bool = False):
+    """Loss and its gradients (dW (L, p, n), dtheta (L,)) for one batch
+    (rounded: the precision model of forward)."""
+    op, st = _precision(rounded)
     K = np.asarray(K, np.float64)
-    Y = np.asarray(Y, np.float64)
-    xs, zs = forward(K, W, theta, Y)
+    xs, zs = forward(K, W, theta, Y, rounded)
+    Y = st(Y)
     L = W.shape[0]
     B = Y.shape[0]
-    g = 2.0 / B * (xs[L] - np.asarray(Xt, np.float64))
+    g = st(2.0 / B * st(xs[L] - st(Xt)))
     dW = np.zeros(W.shape)
     dtheta = np.zeros(L)
     for l in range(L - 1, -1, -1):
-        act = np.abs(zs[l]) > theta[l]
+        act = np.abs(zs[l]) > st(theta[l])
         delta = g * act
         dtheta[l] = -np.sum(delta * np.sign(zs[l]))
-        r = Y - xs[l] @ K.T
-        dW[l] = delta.T @ r
-        g = delta - (delta @ np.asarray(W[l], np.float64)) @ K
+        r = st(Y - st(op(xs[l]) @ op(K).T))
+        dW[l] = st(op(delta).T @ op(r))
+        g = st(delta - st(op(st(op(delta) @ op(W[l]))) @ op(K)))
     return loss(xs[L], Xt), dW, dtheta
 
 

@@ -9,6 +9,20 @@ no decrease of f for 30 iterations).  Nothing here touches the CUDA path.
     python tests/golden/make_golden.py c3b      # the shared-K right-hand sides: c3b_fstar.json
     python tests/golden/make_golden.py c4       # the warm-start test samples: c4_fstar.json
     python tests/golden/make_golden.py c5       # the radius sweep: c5_fstar.json
+    python tests/golden/make_golden.py xstar    # the oracle's solutions x*: xstar_*.npz
+    python tests/golden/make_golden.py homotopy # exact minimisers from the homotopy path
+
+The x* files hold each solution sparsely (indices and values of its nonzero
+entries, FP64), for configs 0-2 and for a seeded sample of the instances of
+the ragged batch, the shared-K right-hand sides, the warm-start test samples
+and the radius sweep.  Each comes from the same oracle run as the stored f*
+(the reference solve for configs 0-2, the floor solve for the rest), so
+f(x*) equals the stored f*.
+
+The homotopy files hold exact minimisers from the oracle's homotopy path
+(oracle/homotopy.py, no iteration): homotopy_small.npz for six small FP64
+problems (workloads.homotopy_case; y stored with them, so that no platform's
+matrix product enters), and xbar_c5.npz for every radius of the radius sweep.
 """
 import json
 import os
@@ -113,8 +127,118 @@ def main_c4():
                    "solver": "oracle.floor_solve"}, fh, indent=0)
 
 
+def _save_sparse(path, xs, meta):
+    """xs: list of FP64 vectors; stored as their nonzero entries."""
+    arrs = {}
+    for i, x in enumerate(xs):
+        nz = np.flatnonzero(x)
+        arrs[f"idx{i}"] = nz.astype(np.int32)
+        arrs[f"val{i}"] = x[nz]
+        arrs[f"p{i}"] = np.array([x.shape[0]])
+    np.savez_compressed(path, count=np.array([len(xs)]), meta=np.array(json.dumps(meta)), **arrs)
+
+
+def load_sparse(path):
+    """(list of dense FP64 vectors, meta dict) from a file written by _save_sparse."""
+    z = np.load(path)
+    xs = []
+    for i in range(int(z["count"][0])):
+        x = np.zeros(int(z[f"p{i}"][0]))
+        x[z[f"idx{i}"]] = z[f"val{i}"]
+        xs.append(x)
+    return xs, json.loads(str(z["meta"]))
+
+
+SAMPLE = 16   # instances per sampled workload
+
+
+def main_xstar(which=("c0", "c1", "c2", "c3a", "c3b", "c4", "c5")):
+    """tests/golden/xstar_<cfg>.npz: the oracle's x* (same solves as the f* files)."""
+    d = os.path.dirname(OUT)
+    gold = json.load(open(OUT))
+    for name in which:
+        t = time.time()
+        if name in CONFIGS:
+            prob = CONFIGS[name]()
+            x, res, _ = oracle.reference_solve(prob)
+            meta = {"workload": prob.name, "f": res.f, "f_star_file": gold[name]["f_star"], "solver": "oracle.reference_solve"}
+            _save_sparse(os.path.join(d, f"xstar_{name}.npz"), [x], meta)
+        elif name == "c3a":
+            sizes = W.ragged_sizes(512)
+            idx = list(range(0, 512, 512 // SAMPLE))
+            xs, fs = [], []
+            for i in idx:
+                x, r, _ = oracle.floor_solve(W.ragged_instance(i, sizes[i]))
+                xs.append(x)
+                fs.append(r.f)
+            _save_sparse(os.path.join(d, "xstar_c3a.npz"), xs, {"instances": idx, "f": fs, "solver": "oracle.floor_solve"})
+        elif name == "c3b":
+            Ks, ldk, Y, rho, X = W.shared_k(nrhs=1024)
+            n, p = Ks.shape[0], X.shape[1]
+            idx = list(range(0, 1024, 1024 // SAMPLE))
+            xs, fs = [], []
+            for b in idx:
+                x, r, _ = oracle.floor_solve(W.Problem(Ks, n, p, ldk, W.DT_BF16, Y[b].copy(), float(rho[b]), X[b], "c3b"))
+                xs.append(x)
+                fs.append(r.f)
+            _save_sparse(os.path.join(d, "xstar_c3b.npz"), xs, {"instances": idx, "f": fs, "solver": "oracle.floor_solve"})
+        elif name == "c4":
+            Ks, ldk, Y, rho, X, ntr = W.warm_start_split()
+            n, p = Ks.shape[0], X.shape[1]
+            nte = Y.shape[0] - ntr
+            idx = list(range(0, nte, nte // SAMPLE))
+            xs, fs = [], []
+            for q in idx:
+                x, r, _ = oracle.floor_solve(W.Problem(Ks, n, p, ldk, W.DT_BF16, Y[ntr + q].copy(), float(rho[ntr + q]),
+                                                       X[ntr + q], "c4"))
+                xs.append(x)
+                fs.append(r.f)
+            _save_sparse(os.path.join(d, "xstar_c4.npz"), xs, {"test_samples": idx, "f": fs, "solver": "oracle.floor_solve"})
+        elif name == "c5":
+            Ks, ldk, n, y, rho, xt = W.rho_sweep()
+            p = xt.shape[0]
+            idx = list(range(0, len(rho), 5))
+            xs, fs = [], []
+            for b in idx:
+                x, r, _ = oracle.floor_solve(W.Problem(Ks, n, p, ldk, W.DT_BF16, y.copy(), float(rho[b]), xt, "c5"))
+                xs.append(x)
+                fs.append(r.f)
+            _save_sparse(os.path.join(d, "xstar_c5.npz"), xs, {"radii": idx, "f": fs, "solver": "oracle.floor_solve"})
+        print(name, f"{time.time() - t:.0f}s", flush=True)
+
+
+HOMOTOPY_CASES = [(0, 30, 60, 6), (1, 30, 60, 6), (2, 40, 120, 8), (3, 50, 40, 5), (4, 20, 200, 4),
+                  (5, 64, 64, 10)]
+
+
+def main_homotopy():
+    """tests/golden/homotopy_small.npz and tests/golden/xbar_c5.npz (exact path points)."""
+    from oracle import homotopy
+    d = os.path.dirname(OUT)
+    t = time.time()
+    arrs = {}
+    for q, (seed, n, p, k) in enumerate(HOMOTOPY_CASES):
+        K, y, rho, _ = W.homotopy_case(seed, n, p, k)
+        xh, lam, segs = homotopy.solve_at_radius(K, y, rho)
+        arrs.update({f"y{q}": y, f"x{q}": xh, f"lam{q}": np.array([lam]), f"rho{q}": np.array([rho])})
+    np.savez_compressed(os.path.join(d, "homotopy_small.npz"), cases=np.array(HOMOTOPY_CASES), **arrs)
+    Ks, ldk, n, y, rho, xt = W.rho_sweep()
+    p = xt.shape[0]
+    sols = homotopy.solve_at_radii(W.bf16_bits_to_f64(Ks[:, :p]), y.astype(np.float64), rho)
+    _save_sparse(os.path.join(d, "xbar_c5.npz"), [s[0] for s in sols],
+                 {"radii": list(range(len(rho))), "lam": [s[1] for s in sols], "segments": [s[2] for s in sols],
+                  "solver": "oracle.homotopy.solve_at_radii"})
+    print("homotopy", f"{time.time() - t:.0f}s", flush=True)
+
+
 if __name__ == "__main__":
     args = sys.argv[1:]
+    if args == ["homotopy"]:
+        main_homotopy()
+        sys.exit(0)
+    if args and args[0] == "xstar":
+        main_xstar(tuple(args[1:]) or ("c0", "c1", "c2", "c3a", "c3b", "c4", "c5"))
+        sys.exit(0)
     if args == ["c4"]:
         main_c4()
         sys.exit(0)

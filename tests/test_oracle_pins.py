@@ -18,9 +18,16 @@ error in the soft threshold, an Armijo test with the wrong sign.
     - the KKT sign conditions on the configurations;
     - a 3-iteration trace on a diagonal problem derived by hand (below);
     - monotone decrease (M = 1), feasibility, steplength bounds.
+* The comparison methods of Sec. 2 (oracle/methods.py): ISTA/FISTA and PSD in
+  one step on an orthonormal K (closed forms of eq. 1 and eq. 2), a PSD step
+  on a diagonal K derived by hand, FISTA's first step and momentum weight, and
+  all three at the exact homotopy points.
+* The learned warm start (oracle/lista.py) and the homotopy path
+  (oracle/homotopy.py): see their sections below.
 """
 import itertools
 import json
+import sys
 import os
 
 import numpy as np
@@ -28,8 +35,10 @@ import pytest
 
 import oracle
 import workloads as W
+from oracle import methods
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+sys.path.insert(0, GOLDEN)
 
 
 # ----------------------------------------------------------------- helpers
@@ -116,23 +125,9 @@ def brute_eq2(K, y, rho):
 
 
 def fista(K, y, lam, iters):
-    """FISTA (eq. fista) for min ||Kx - y||^2 + 2 lam ||x||_1, step 1/||K||^2.
-
-    With ||K|| = 1 this is exactly the paper's iteration x <- T(x + ...) with
-    T(x) = S_lam[x + K^T (y - K x)]; here K is rescaled through the step.
-    """
-    L = np.linalg.norm(K, 2) ** 2
-    x = np.zeros(K.shape[1])
-    x_prev = x.copy()
-    t = 1.0
-    for _ in range(iters):
-        t_next = (1 + np.sqrt(1 + 4 * t * t)) / 2
-        u = x + (t - 1) / t_next * (x - x_prev)
-        w = u + K.T @ (y - K @ u) / L
-        x_prev = x
-        x = np.sign(w) * np.maximum(np.abs(w) - lam / L, 0)
-        t = t_next
-    return x
+    """FISTA (eq. fista) for min ||Kx - y||^2 + 2 lam ||x||_1 with step 1/||K||^2
+    (oracle/methods.py; with ||K|| = 1 the paper's iteration itself)."""
+    return methods.ista(K, y, lam, iters, step=1.0 / np.linalg.norm(K, 2) ** 2, fista=True)[0]
 
 
 def dense_problem(K, y, rho):
@@ -411,6 +406,81 @@ def test_lista_backward_matches_finite_differences():
         assert abs((fp - fm) / (2 * h) - dth[l]) <= 1e-6 * max(1.0, abs(dth[l]))
 
 
+def test_lista_bf16_rounding_is_round_to_nearest_even():
+    """The precision model's rounding against torch's float32 -> bfloat16
+    conversion (round to nearest, ties to even), bit for bit, including ties."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(41)
+    a = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-6, 6, 4000),
+                        1.0 + np.arange(-8, 9) * 2.0 ** -8,            # ties at 1 + odd * 2^-8
+                        1.0 + np.arange(-8, 9) * 2.0 ** -9])
+    a = a.astype(np.float32).astype(np.float64)
+    ref = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(lista.bf16(a), ref)
+    assert lista.bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0                        # tie to even (down)
+    assert lista.bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6        # tie to even (up)
+
+
+def test_lista_precision_model_is_exact_on_representable_data():
+    """With small sparse integers everywhere (every operand and every sum below
+    2^8, so exactly representable in BF16 and FP32), the rounded network equals
+    the FP64 network exactly, forward and backward: the model rounds only where
+    a tensor-core implementation does, and never changes a representable value."""
+    rng = np.random.default_rng(0)
+    n, p, L, B = 4, 5, 2, 2
+    K = rng.integers(-1, 2, (n, p)).astype(np.float64) * (rng.random((n, p)) < 0.6)
+    W = rng.integers(-1, 2, (L, p, n)).astype(np.float64) * (rng.random((L, p, n)) < 0.6)
+    Y = rng.integers(-3, 4, (B, n)).astype(np.float64)
+    Xt = rng.integers(-2, 3, (B, p)).astype(np.float64)
+    theta = np.array([1.0, 1.0])
+    x64 = lista.forward(K, W, theta, Y)[0][-1]
+    x16 = lista.forward(K, W, theta, Y, rounded=True)[0][-1]
+    assert np.array_equal(x64, x16) and np.abs(x64).max() > 0
+    l64, dW64, dt64 = lista.backward(K, W, theta, Y, Xt)
+    l16, dW16, dt16 = lista.backward(K, W, theta, Y, Xt, rounded=True)
+    assert np.abs(dW64).max() > 0 and np.count_nonzero(dt64) == L
+    assert l64 == l16 and np.array_equal(dW64, dW16) and np.array_equal(dt64, dt16)
+
+
+def test_lista_exact_case_loses_nothing_to_rounding():
+    """The data of the kernels' exact LISTA test (workloads.lista_exact_case,
+    K 64 x 128, batch 64, two layers): the BF16 precision model equals the FP64
+    network exactly, forward and backward, with both layers active (between a
+    third and a half of the pre-threshold values above theta) and every dW row
+    touched.  Its values are multiples of 2^-10 below 2^8 in size (at most 18
+    significant bits; the sums of the magnitudes of the terms of every product
+    stay below 2^8 too, 173 at most for dtheta), so FP32 sums of them are exact
+    in any order."""
+    K, Wl, theta, Y, Xt = W.lista_exact_case()
+    xs, zs = lista.forward(K, Wl, theta, Y)
+    xr, _ = lista.forward(K, Wl, theta, Y, rounded=True)
+    assert all(np.array_equal(a, b) for a, b in zip(xs, xr))
+    for z, t in zip(zs, theta):
+        assert 0.3 < np.mean(np.abs(z) > t) < 0.6
+    l64, dW64, dt64 = lista.backward(K, Wl, theta, Y, Xt)
+    l16, dW16, dt16 = lista.backward(K, Wl, theta, Y, Xt, rounded=True)
+    assert l64 == l16 and np.array_equal(dW64, dW16) and np.array_equal(dt64, dt16)
+    assert np.all(np.abs(dW64).max(axis=2) > 0)
+    for v in (*xs, *zs, dW64, dt64):
+        assert np.all(v * 2.0 ** 10 == np.round(v * 2.0 ** 10)) and np.abs(v).max() < 2.0 ** 8
+
+
+def test_lista_precision_model_within_bf16_error_of_fp64():
+    """On random data the rounded network differs from the FP64 one by about the
+    BF16 unit roundoff (2^-9) compounded over the layers, and not by less than
+    a rounding: the model does round."""
+    rng = np.random.default_rng(43)
+    n, p, L, B = 32, 96, 4, 8
+    K = rng.standard_normal((n, p)) / np.sqrt(n)
+    W0, th, _ = lista.init_params(K, L, 0.05)
+    W = W0 * (1 + 0.2 * rng.standard_normal(W0.shape))
+    Y = rng.standard_normal((B, n))
+    x64 = lista.forward(K, W, th, Y)[0][-1]
+    x16 = lista.forward(K, W, th, Y, rounded=True)[0][-1]
+    rel = np.linalg.norm(x16 - x64) / np.linalg.norm(x64)
+    assert 1e-5 < rel < 4 * L * 2.0 ** -9, rel
+
+
 def test_nonmonotone_line_search_invariant():
     """M > 1 (the nonmonotone Armijo rule of Alg. GP, Step 4): every accepted value
     lies below the largest of the last M (gT d < 0), f need not decrease at every
@@ -478,3 +548,99 @@ def test_homotopy_path_is_piecewise_linear_and_monotone():
         if np.array_equal(np.sign(x0), np.sign(x1)) and np.array_equal(np.sign(x1), np.sign(x2)):
             t = (r1 - r0) / (r2 - r0)
             assert np.linalg.norm(x1 - ((1 - t) * x0 + t * x2)) <= 1e-10 * np.linalg.norm(x1)
+
+
+# ------------------------------------------------------- comparison methods (Sec. 2)
+
+
+def _homotopy_stored(case):
+    z = np.load(os.path.join(os.path.dirname(__file__), "golden", "homotopy_small.npz"))
+    return z[f"y{case}"], z[f"x{case}"], float(z[f"lam{case}"][0]), float(z[f"rho{case}"][0])
+
+
+def test_ista_fista_one_step_on_orthonormal_k_is_the_closed_form():
+    """K^T K = I: eq. 1 separates into p scalar problems x_i^2 - 2 x_i b_i +
+    2 lam |x_i| (b = K^T y), minimised by the soft threshold S_lam(b_i).  From any
+    x0 one ISTA or FISTA step (s = 1) lands there and stays: K^T K x0 = x0
+    cancels the starting point, and T is constant on such a K."""
+    prob = W.orthonormal(200, 80, 10, seed=4)
+    K = prob.K_f64()
+    b = K.T @ prob.y
+    lam = 0.3 * np.abs(b).max()
+    xs = np.sign(b) * np.maximum(np.abs(b) - lam, 0.0)
+    # the scalar problems' minimiser, checked against a fine grid for a few entries
+    for i in np.argsort(-np.abs(b))[:3]:
+        grid = np.linspace(-2 * abs(b[i]), 2 * abs(b[i]), 40001)
+        obj = grid ** 2 - 2 * grid * b[i] + 2 * lam * np.abs(grid)
+        assert abs(grid[np.argmin(obj)] - xs[i]) <= 4 * abs(b[i]) / 40000
+    x0 = np.random.default_rng(5).standard_normal(80)
+    for fista in (False, True):
+        for iters in (1, 3):
+            x, tr = methods.ista(K, prob.y, lam, iters, step=1.0, x0=x0, fista=fista)
+            np.testing.assert_allclose(x, xs, atol=1e-12 * np.abs(b).max())
+    assert np.count_nonzero(xs) > 0
+
+
+def test_fista_first_step_equals_ista_and_momentum_follows_t():
+    """t^(0) = 1 gives no momentum in the first step, so FISTA's x^(1) is ISTA's;
+    the second step's extrapolation weight is (t^(1) - 1)/t^(2) with
+    t^(1) = (1 + sqrt 5)/2 and t^(2) = (1 + sqrt(1 + 4 t1^2))/2."""
+    rng = np.random.default_rng(6)
+    K = rng.standard_normal((20, 50)) / np.sqrt(20) / 3.0
+    y = rng.standard_normal(20)
+    lam = 0.05
+    xi, _ = methods.ista(K, y, lam, 1)
+    xf, _ = methods.ista(K, y, lam, 1, fista=True)
+    assert np.array_equal(xi, xf)
+    t1 = (1 + np.sqrt(5.0)) / 2
+    t2 = (1 + np.sqrt(1 + 4 * t1 * t1)) / 2
+    u = xf + (t1 - 1) / t2 * (xf - 0.0)
+    x2 = methods.soft(u + K.T @ (y - K @ u), lam)
+    np.testing.assert_allclose(methods.ista(K, y, lam, 2, fista=True)[0], x2, rtol=0, atol=1e-15)
+
+
+def test_psd_hand_derived_step_on_a_diagonal_k():
+    """K = diag(1, 2), y = (1, 1), x0 = 0: r = K^T y = (1, 2), ||r||^2 = 5,
+    K r = (1, 4), ||K r||^2 = 17, beta = 5/17, x0 + beta r = (5/17, 10/17).
+    rho = 10: inside the ball, x1 = (5/17, 10/17).  rho = 1/2: the projection
+    subtracts tau = (15/17 - 1/2)/2 = 13/68 from both, x1 = (7/68, 27/68)."""
+    K = np.diag([1.0, 2.0])
+    y = np.array([1.0, 1.0])
+    x, tr = methods.psd(K, y, 10.0, 1)
+    assert abs(tr[0, 2] - 5 / 17) <= 1e-15 and abs(tr[0, 0] - 2.0) <= 1e-15
+    np.testing.assert_allclose(x, [5 / 17, 10 / 17], rtol=0, atol=1e-15)
+    x, _ = methods.psd(K, y, 0.5, 1)
+    np.testing.assert_allclose(x, [7 / 68, 27 / 68], rtol=0, atol=1e-15)
+
+
+def test_psd_one_step_on_orthonormal_k_is_the_closed_form():
+    """K^T K = I: ||K r|| = ||r||, so beta = 1 and x1 = P(x0 + K^T y - x0) =
+    P(K^T y), the minimiser of eq. 2 (threshold by bisection, not the oracle's
+    projection)."""
+    prob = W.orthonormal(300, 120, 15, seed=3, rho_scale=0.5)
+    K = prob.K_f64()
+    xs, tau = soft_threshold_bisect(K.T @ prob.y, prob.rho)
+    x, tr = methods.psd(K, prob.y, prob.rho, 1)
+    assert abs(tr[0, 2] - 1.0) <= 1e-12
+    np.testing.assert_allclose(x, xs, atol=1e-12 * np.abs(xs).max())
+
+
+@pytest.mark.parametrize("case", [0, 2, 4])
+def test_methods_reach_the_exact_homotopy_points(case):
+    """On the stored homotopy problems: ISTA and FISTA (step 1/||K||^2) reach
+    x-bar(lam), the minimiser of eq. 1 at the stored lam; PSD reaches the
+    minimiser of eq. 2 at the stored radius, which is the same point (the
+    relation of Sec. 1)."""
+    from make_golden import HOMOTOPY_CASES
+    seed, n, p, k = HOMOTOPY_CASES[case]
+    K, _, _, _ = W.homotopy_case(seed, n, p, k)
+    y, xh, lam, rho = _homotopy_stored(case)
+    s = 1.0 / np.linalg.norm(K, 2) ** 2
+    xf, trf = methods.ista(K, y, lam, 20000, step=s, fista=True)
+    xi, tri = methods.ista(K, y, lam, 60000, step=s)
+    xp, trp = methods.psd(K, y, rho, 20000)
+    for x in (xf, xi, xp):
+        assert np.linalg.norm(x - xh) <= 1e-7 * np.linalg.norm(xh), np.linalg.norm(x - xh) / np.linalg.norm(xh)
+    F = methods.penalised(K, y, lam, xh)
+    assert trf[-1, 1] <= F * (1 + 1e-12) and tri[-1, 1] <= F * (1 + 1e-12)
+    assert np.all(np.diff(tri[:, 1]) <= 1e-12 * F)      # ISTA decreases eq. 1 monotonically

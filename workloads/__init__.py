@@ -238,6 +238,41 @@ def warm_start_train(count: int = 65536, n: int = 1024, p: int = 4096, k: int = 
     return Y, rho
 
 
+def lista_exact_case(seed: int = 3, n: int = 64, p: int = 128, B: int = 64, L: int = 2):
+    """Learned-warm-start data on which BF16 operands and FP32 sums lose nothing:
+    K with one +-1 per column, W_l with one entry in {+-1, +-1/2} per row, y
+    integers in [-3, 3] (half of them zero), thresholds 3/4, targets multiples of
+    1/4.  Every value the network and its gradient form is then a short dyadic
+    fraction, so a BF16/FP32 implementation must return the FP64 values exactly
+    (the default seed is one for which that holds).  Returns (K, W, theta, Y, Xt)
+    in float64."""
+    rng = np.random.default_rng(seed)
+    K = np.zeros((n, p))
+    rows = rng.integers(0, n, size=p)
+    K[rows, np.arange(p)] = rng.choice([-1.0, 1.0], size=p)
+    W = np.zeros((L, p, n))
+    for l in range(L):
+        for i in range(p):
+            col = rng.integers(0, n)
+            W[l, i, col] = rng.choice([-1.0, 1.0, 0.5, -0.5])
+    Y = rng.integers(-3, 4, size=(B, n)).astype(np.float64) * (rng.random((B, n)) < 0.5)
+    theta = np.full(L, 0.75)
+    Xt = rng.integers(-2, 3, size=(B, p)).astype(np.float64) * 0.25 * (rng.random((B, p)) < 0.3)
+    return K, W, theta, Y, Xt
+
+
+def homotopy_case(seed: int, n: int, p: int, k: int):
+    """A small FP64 problem for the exact homotopy reference: K n x p N(0, 1/n),
+    k-sparse N(0,1) signal, noise 0.01, rho = 0.8 ||x_true||_1.  Returns
+    (K, y, rho, x_true)."""
+    rng = np.random.default_rng(seed)
+    K = rng.standard_normal((n, p)) / np.sqrt(n)
+    xt = np.zeros(p)
+    xt[rng.choice(p, k, replace=False)] = rng.standard_normal(k)
+    y = K @ xt + 0.01 * rng.standard_normal(n)
+    return K, y, 0.8 * float(np.abs(xt).sum()), xt
+
+
 def rho_sweep(n: int = 1848, p: int = 8192, k: int = 120, count: int = 50, *, seed: int = SEED_BASE + 7,
               noise: float = 0.02, lo: float = 0.05, hi: float = 1.0):
     """The paper's Gaussian test shape (Sec. 4) as a sweep over the radius: K
