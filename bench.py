@@ -366,99 +366,116 @@ def run_shared_k(nrhs, dev, verify=16, plain=8, pin=None):
 
 
 # ------------------------------------------------ learned warm start (c4)
-def run_warm_start(dev, steps=3000, batch=256, ntrain=65536, lr=3e-4):
-    """The learned warm start on K 1024 x 4096 (BF16): `ntrain` training right-hand
-    sides (workloads.warm_start_train) with the solver's own solutions as targets
-    (shared-K form), the network (6 layers, W_l initialised to K^T / ||K||^2,
-    theta_l to the median lambda / ||K||^2) trained with Adam on the GPU, and the
-    test samples solved to relative gap 1e-6 (kernel stop 5e-7, stored oracle
-    optima) from x0 = 0 (cold) and from the projected network output (warm,
-    inference included; alpha_0 from the projected-gradient step at x0, rule 1)."""
+def run_warm_start(dev, steps=3000, batch=256, lr=3e-4, plain_sample=512, verify=64):
+    """The learned warm start at its full configuration (K 1024 x 4096 BF16): 10^5
+    training right-hand sides (workloads.warm_start_train) with the solver's own
+    solutions as targets (shared-K form, 120 iterations), the network initialised by
+    gpl1_lista_init (6 layers, W_l = K^T / L, theta_l = median lambda / L) and
+    trained with Adam on the GPU (gpl1_lista_train), then the 10^4 test right-hand
+    sides (workloads.warm_start_test) solved to relative gap 1e-6 (kernel stop 5e-7
+    against the oracle's optima, tests/golden/c4full_fstar.json) three ways: plain
+    (one gpl1_solve per instance, timed on a sample), batched cold (shared-K form
+    from x0 = 0) and batched warm (gpl1_solve_warm: inference, warm solve, and the
+    cold fallback for any instance the warm solve leaves unconverged).  A spread
+    sample of the returned x is checked in FP64."""
     import torch
 
     import paper_0902_4424_gb300 as pkg
     import workloads as W
-    with open(os.path.join(ROOT, "tests", "golden", "c4_fstar.json")) as fh:
-        gold = json.load(fh)
-    Ks, ldk, Y, rho, Xt, ntr0 = W.warm_start_split()
-    n, p = Ks.shape[0], Xt.shape[1]
-    nte = Y.shape[0] - ntr0
-    fstars = gold["f_star"]
-    Ytr, rho_tr = W.warm_start_train(ntrain, n, p)
+    with open(os.path.join(ROOT, "tests", "golden", "c4full_fstar.json")) as fh:
+        fstars = json.load(fh)["f_star"]
+    Ks, ldk = W.warm_start_K()
+    n, p = Ks.shape[0], 4096
+    Ytr, rho_tr = W.warm_start_train(W.WARM_TRAIN_FULL, n, p)
+    Yte, rho_te = W.warm_start_test(W.WARM_TEST_FULL, n, p)
+    ntr, nte = Ytr.shape[0], Yte.shape[0]
     K = torch.from_numpy(Ks.view(np.int16)).to(dev)
-    # training samples first, then the test samples (the last rows of the split)
-    Yd = torch.from_numpy(np.ascontiguousarray(np.concatenate([Ytr, Y[ntr0:]]))).to(dev)
-    rho = np.concatenate([rho_tr, rho[ntr0:]])
-    ntr = ntrain
+    Ytr_d = torch.from_numpy(Ytr).to(dev)
+    Yte_d = torch.from_numpy(Yte).to(dev)
     ctx = pkg.Context(dev.index or 0)
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+    chunk = 4096
+
+    def timed(fn):
+        a, b = ev(), ev()
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return out, a.elapsed_time(b)
+
     # training targets: solutions of eq. 2 for the training samples (shared-K form)
-    a, b = ev(), ev()
-    a.record(stream)
-    targets, lams = [], []
-    for c0 in range(0, ntr, 4096):
-        Xs, res = ctx.solve_shared_k(K, Yd[c0:c0 + 4096], rho[c0:c0 + 4096], p=p,
-                                     params=pkg.params_default(stop_rule=0, max_iter=120))
-        targets.append(Xs)
-        lams += [r.lambda_ for r in res]
-    Xtr = torch.cat(targets)
-    b.record(stream)
-    b.synchronize()
-    target_ms = a.elapsed_time(b)
-    # network: W_l = K^T / L, theta_l = median(lambda) / L, L = ||K||_2^2
-    K64 = W.bf16_bits_to_f64(Ks[:, :p])
-    Lk = float(np.linalg.norm(K64, 2) ** 2)
+    def targets():
+        xs, lams = [], []
+        for c0 in range(0, ntr, chunk):
+            Xs, res = ctx.solve_shared_k(K, Ytr_d[c0:c0 + chunk], rho_tr[c0:c0 + chunk], p=p,
+                                         params=pkg.params_default(stop_rule=0, max_iter=120))
+            xs.append(Xs)
+            lams += [r.lambda_ for r in res]
+        return torch.cat(xs), lams
+    (Xtr, lams), target_ms = timed(targets)
     layers = 6
-    Wd = (torch.from_numpy((K64.T / Lk).astype(np.float32)).to(dev)).unsqueeze(0).repeat(layers, 1, 1).contiguous()
-    thd = torch.full((layers,), float(np.median(lams)) / Lk, dtype=torch.float32, device=dev)
+    (Wd, thd, Lk), init_ms = timed(lambda: ctx.lista_init(K, layers, lams, p=p))
     m = torch.zeros(layers * p * n + layers, dtype=torch.float32, device=dev)
     v = torch.zeros_like(m)
-    a, b = ev(), ev()
-    a.record(stream)
-    losses = ctx.lista_train(K, Wd, thd, m, v, Yd[:ntr], Xtr, batch=batch, steps=steps, lr=lr, lr_theta=lr)
-    b.record(stream)
-    b.synchronize()
-    train_ms = a.elapsed_time(b)
-    # test: cold and warm solves of the test samples
+    losses, train_ms = timed(lambda: ctx.lista_train(K, Wd, thd, m, v, Ytr_d, Xtr, batch=batch, steps=steps, lr=lr,
+                                                     lr_theta=lr))
+    del Xtr
     prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=0.5 * TOL, max_iter=5000)
-    Yte = Yd[ntr:]
-    ctx.solve_shared_k(K, Yte, rho[ntr:], p=p, f_star=fstars, params=prm)   # warm-up
-    a, b = ev(), ev()
-    a.record(stream)
-    Xc, rc = ctx.solve_shared_k(K, Yte, rho[ntr:], p=p, f_star=fstars, params=prm)
-    b.record(stream)
-    b.synchronize()
-    cold_ms = a.elapsed_time(b)
-    prm_w = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=0.5 * TOL, max_iter=5000, alpha0_rule=1)
-    a, b = ev(), ev()
-    a.record(stream)
-    X0 = ctx.lista_forward(K, Wd, thd, Yte)
-    Xw, rw = ctx.solve_shared_k(K, Yte, rho[ntr:], p=p, f_star=fstars, params=prm_w, X=X0)
-    b.record(stream)
-    b.synchronize()
-    warm_ms = a.elapsed_time(b)
-    # the network's output (the solve above overwrote X0) against the solutions, on the test samples
-    Xn = ctx.lista_forward(K, Wd, thd, Yte)
-    test_rel_err = float((((Xn - Xc) ** 2).sum(1).mean() / (Xc ** 2).sum(1).mean()).sqrt().item())
-    probs = [W.Problem(Ks, n, p, ldk, W.DT_BF16, Y[ntr0 + q].copy(), float(rho[ntr + q]), Xt[ntr0 + q], "c4")
-             for q in range(nte)]
-    Xwh = Xw.double().cpu().numpy()
-    idx = np.linspace(0, nte - 1, 16).astype(int)
-    gaps = [(objective_f64(probs[q], Xwh[q]) - fstars[q]) / fstars[q] for q in idx]
+
+    def cold():
+        xs, rs = [], []
+        for c0 in range(0, nte, chunk):
+            Xc, rc = ctx.solve_shared_k(K, Yte_d[c0:c0 + chunk], rho_te[c0:c0 + chunk], p=p,
+                                        f_star=fstars[c0:c0 + chunk], params=prm)
+            xs.append(Xc)
+            rs += rc
+        return torch.cat(xs), rs
+    cold()   # warm-up and GEMM tuning
+    (Xc, rc), cold_ms = timed(cold)
+    warm = lambda: ctx.solve_warm(K, Wd, thd, Yte_d, rho_te, f_star=fstars, params=prm)   # noqa: E731
+    warm()
+    (Xw, rw, fb, nfb), warm_ms = timed(warm)
+    # plain: one gpl1_solve per instance, on a spread sample
+    idx = np.linspace(0, nte - 1, plain_sample).astype(int)
+    x1 = torch.zeros(p, dtype=torch.float32, device=dev)
+
+    def plain():
+        its = []
+        for q in idx:
+            _, r = ctx.solve(K, Yte_d[q], float(rho_te[q]), x=x1, p=p,
+                             params=pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=0.5 * TOL,
+                                                       f_star=fstars[q], x0_is_zero=1, max_iter=5000))
+            its.append(r.iters)
+        return its
+    plain()
+    plain_its, plain_ms = timed(plain)
+    # the network's output against the cold solutions, and the FP64 check of a sample
+    Xn = ctx.lista_forward(K, Wd, thd, Yte_d[:4096])
+    test_rel_err = float((((Xn - Xc[:4096]) ** 2).sum(1).mean() / (Xc[:4096] ** 2).sum(1).mean()).sqrt().item())
+    vidx = np.linspace(0, nte - 1, verify).astype(int)
+    Xwh = Xw[vidx].double().cpu().numpy()
+    gaps = []
+    for j, q in enumerate(vidx):
+        pr = W.Problem(Ks, n, p, ldk, W.DT_BF16, Yte[q].copy(), float(rho_te[q]), None, "c4")
+        gaps.append((objective_f64(pr, Xwh[j]) - fstars[q]) / fstars[q])
     ctx.close()
     return {"workload": f"c4_warmstart{n}x{p}_bf16", "train_samples": ntr, "test_samples": nte,
-            "layers": layers, "train_steps": steps, "batch": batch, "train_ms": train_ms,
-            "target_solve_ms": target_ms, "loss_first": float(np.mean(losses[:8])),
-            "loss_last": float(np.mean(losses[-8:])),
+            "layers": layers, "train_steps": steps, "batch": batch, "spectral_norm_sq": Lk,
+            "target_solve_ms": target_ms, "init_ms": init_ms, "train_ms": train_ms,
+            "loss_first": float(np.mean(losses[:8])), "loss_last": float(np.mean(losses[-8:])),
             "test_rel_err": test_rel_err,
+            "plain_solves_per_s": len(idx) / (plain_ms / 1e3), "plain_iters_mean": statistics.mean(plain_its),
+            "plain_sample": len(idx),
             "cold_solves_per_s": nte / (cold_ms / 1e3), "warm_solves_per_s": nte / (warm_ms / 1e3),
             "cold_iters_mean": statistics.mean(r.iters for r in rc),
             "warm_iters_mean": statistics.mean(r.iters for r in rw),
             "cold_ok": sum(r.status == 0 for r in rc), "warm_ok": sum(r.status == 0 for r in rw),
-            "warm_verified_max_rel_gap": max(gaps), "verified_instances": len(gaps),
+            "fallbacks": nfb, "warm_verified_max_rel_gap": max(gaps), "verified_instances": len(gaps),
             "stop": f"kernel stop rel_gap<={0.5 * TOL:g} vs oracle f* per test sample",
-            "note": "warm time includes the network's inference; both solved in one shared-K call"}
+            "note": "warm time includes the network's inference and the cold fallbacks; batched forms in "
+                    "shared-K calls of 4096 right-hand sides"}
 
 
 # ------------------------------------------------ radius sweep (c5)
@@ -522,19 +539,26 @@ def run_rho_sweep(dev):
         g = gaps(torch.stack(xs).double().cpu().numpy())
         out[mode] = {"solves_per_s": R / (ms / 1e3), "ms": ms, "iters_mean": statistics.mean(its), "ok": oks,
                      "verified_max_rel_gap": max(g)}
-    # isochrones: all radii under a fixed iteration budget (no stop rule), the time of
-    # the call and the gap each radius reached
+    # isochrones (Sec. 4): all radii under a fixed iteration budget (no stop rule), the
+    # time of the call, and per radius the relative error ||x - x_bar|| / ||x_bar||
+    # against the exact point of the homotopy path (tests/golden/xbar_c5.npz) and the gap
+    import sys as _sys
+    _sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    from make_golden import load_sparse
+    xbar = load_sparse(os.path.join(ROOT, "tests", "golden", "xbar_c5.npz"))[0]
     iso = []
-    for budget in (4, 8, 16, 32):
+    for budget in (4, 8, 16, 32, 64, 128):
         prm_b = pkg.params_default(stop_rule=0, max_iter=budget)
         a, b = ev(), ev()
         a.record(stream)
         Xb, _ = ctx.solve_shared_k(K, Yd, rho, p=p, params=prm_b)
         b.record(stream)
         b.synchronize()
-        g = gaps(Xb.double().cpu().numpy())
-        iso.append({"iterations": budget, "ms": a.elapsed_time(b), "gap_median": float(np.median(g)),
-                    "gap_max": float(max(g))})
+        Xh = Xb.double().cpu().numpy()
+        g = gaps(Xh)
+        err = [float(np.linalg.norm(Xh[q] - xbar[q]) / np.linalg.norm(xbar[q])) for q in range(R)]
+        iso.append({"iterations": budget, "ms": a.elapsed_time(b), "x_err_median": float(np.median(err)),
+                    "x_err_max": float(max(err)), "gap_median": float(np.median(g)), "gap_max": float(max(g))})
     out["isochrones"] = iso
     out["stop"] = f"kernel stop gap<={0.5 * TOL:g} vs oracle f* per radius, relative to max(f*, 1e-6 ||y||^2)"
     ctx.close()
@@ -696,13 +720,14 @@ def run_ours(args, rank, world, local_rank):
     if args.extras:
         line["two_pass"] = run_engine_compare(ctx, K, y, prob, prm, flush, args.steps, dev)
         line["fw_stop"] = run_fw_stop(ctx, K, y, prob, fstar, flush, args.steps, dev)
+        line["methods"] = run_methods(ctx, K, y, prob, flush, min(args.steps, 5), dev)
         line["c0"] = run_small_config("c0", dev, 20)
         line["c2"] = run_small_config("c2", dev, 10)
     if args.batched_sample > 0:
         line["batched"] = run_batched(args.batched_sample, 3, dev)
     if args.shared_k > 0 and os.path.exists(os.path.join(ROOT, "tests", "golden", "c3b_fstar.json")):
         line["shared_k"] = run_shared_k(args.shared_k, dev, pin=args.shared_k_pin)
-    if args.warm_start and os.path.exists(os.path.join(ROOT, "tests", "golden", "c4_fstar.json")):
+    if args.warm_start and os.path.exists(os.path.join(ROOT, "tests", "golden", "c4full_fstar.json")):
         line["warm_start"] = run_warm_start(dev)
     if args.rho_sweep and os.path.exists(os.path.join(ROOT, "tests", "golden", "c5_fstar.json")):
         line["rho_sweep"] = run_rho_sweep(dev)
@@ -770,6 +795,56 @@ def run_fw_stop(ctx, K, y, prob, fstar, flush, steps, dev):
                                "iters_per_solve": statistics.mean(r.iters for r in res),
                                "stop_reasons": sorted({pkg.STOP[r.stop] for r in res}),
                                "verified_rel_gap": gap, "ok": sum(r.status == 0 for r in res)}
+    return out
+
+
+def run_methods(ctx, K, y, prob, flush, steps, dev):
+    """The comparison methods of Sec. 2 on the same kernel and workload (c1), next to
+    Alg. GP + SS: ISTA and FISTA on eq. 1 at the lambda of the lambda-rho relation
+    (stored with f*) with step 1/||K||^2 (gpl1_spectral_norm_sq, timed apart), and
+    PSD on eq. 2.  Each stops at the distance to its optimum the GPSS solve stops
+    at, ||K (x - x*)||^2 <= 5e-7 f*: relative gap 5e-7 in f for GPSS and PSD, the
+    same absolute gap in eq. 1's objective (optimum f* + 2 lambda rho) for ISTA and
+    FISTA.  Reported per method: solves/s, iterations, passes over K (PSD takes two
+    per iteration) and the x error against the oracle's x*."""
+    import sys as _sys
+
+    import torch
+
+    import paper_0902_4424_gb300 as pkg
+    _sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    from make_golden import load_sparse
+    gold = golden("c1")
+    lam, fs = gold["lambda"], gold["f_star"]
+    xs = load_sparse(os.path.join(ROOT, "tests", "golden", "xstar_c1.npz"))[0][0]
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    L = ctx.spectral_norm_sq(K, pkg.F32, p=prob.p, iters=100)
+    b.record(stream)
+    b.synchronize()
+    out = {"workload": prob.name, "lambda": lam, "spectral_norm_sq": L, "spectral_norm_ms": a.elapsed_time(b),
+           "stop": "||K(x - x*)||^2 <= 5e-7 f* (rel gap 5e-7 in f; eq. 1: the same absolute gap)"}
+    Fs = fs + 2.0 * lam * prob.rho
+    for name, method in (("gpss", pkg.METHOD_GPSS), ("ista", pkg.METHOD_ISTA), ("fista", pkg.METHOD_FISTA),
+                         ("psd", pkg.METHOD_PSD)):
+        if method in (pkg.METHOD_ISTA, pkg.METHOD_FISTA):
+            kw = dict(f_star=Fs, tol=5e-7 * fs / Fs, lambda_pen=lam, step=1.0 / L)
+        else:
+            kw = dict(f_star=fs, tol=5e-7)
+        prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, x0_is_zero=1, max_iter=20000, method=method,
+                                 engine=pkg.ENGINE_ONE_READ, **kw)
+        timed_solves(ctx, K, y, prob, prm, flush, 1, dev)
+        ms, res = timed_solves(ctx, K, y, prob, prm, flush, steps, dev)
+        x, r = ctx.solve(K, y, prob.rho, p=prob.p, params=prm)
+        torch.cuda.synchronize()
+        xh = x.double().cpu().numpy()
+        iters = statistics.mean(q.iters for q in res)
+        out[name] = {"solves_per_s": 1e3 / statistics.mean(ms), "ms_per_solve": statistics.mean(ms),
+                     "iters_per_solve": iters,
+                     "passes_per_solve": (2 * iters if method == pkg.METHOD_PSD else iters) + 1,
+                     "x_rel_err": float(np.linalg.norm(xh - xs) / np.linalg.norm(xs)),
+                     "ok": sum(q.status == 0 for q in res)}
     return out
 
 

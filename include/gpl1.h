@@ -89,25 +89,62 @@ typedef struct {
                           timeout_ns: a fault-free test of the bounded-wait path.      */
   long long timeout_ns; /* bound on every device-side wait                             */
   int engine;          /* which kernel runs a single solve (gpl1_solve, gpl1_solve_async):
-                          GPL1_ENGINE_AUTO picks the one-read kernel when the instance
-                          fits it (p up to 16 slices of 2048 F32 / 4096 BF16 / 1024 F64
-                          columns, or twice that in two chunks per thread) and the
-                          two-pass kernel otherwise; the batched calls and
+                          GPL1_ENGINE_AUTO lets the autotuner pick among the kernels
+                          that can take the instance (below); the batched calls and
                           gpl1_solve_noalloc always run the two-pass kernel          */
-  int engine_pad;      /* 0                                                             */
+  int method;          /* GPL1_METHOD_GPSS (Alg. GP + SS, the default) or one of the
+                          comparison methods of Sec. 2 below; those run only in single
+                          solves (gpl1_solve, gpl1_solve_async) on the one-read kernel */
+  double lambda_pen;   /* ISTA, FISTA: lambda > 0 of eq. 1                             */
+  double step;         /* ISTA, FISTA: step s > 0 of x + s K^T (y - K x) thresholded at
+                          s lambda; 1 is the paper's iteration (||K|| < 1), 1/||K||^2
+                          (gpl1_spectral_norm_sq) admits any K                         */
 } gpl1_params;
+
+/* gpl1_params.method: the iterations of Sec. 2 on the one-read kernel's passes
+ * (each pass forms K v and 2 K^T (K x - y), 2 K^T K v for the pass's direction v
+ * in one read of K; the methods differ only in the scalar step between passes).
+ *  ISTA:  x_{k+1} = S_{s lam}[x_k + s K^T (y - K x_k)]                  (eq. 1)
+ *  FISTA: x_{k+1} = T(x_k + (t_k - 1)/t_{k+1} (x_k - x_{k-1})), T the ISTA map,
+ *         t_0 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2        (eq. fista; eq. 1)
+ *  PSD:   x_{k+1} = P_Omega[x_k + beta_k r_k], r_k = K^T (y - K x_k),
+ *         beta_k = ||r_k||^2 / ||K r_k||^2                                   (eq. 2)
+ * One pass per iteration for ISTA and FISTA, two for PSD (beta_k needs K r_k
+ * before the step).  For ISTA and FISTA, rho is not used (it must still be > 0),
+ * x0 is not projected, f_star is the optimal value of eq. 1 (||K x - y||^2 +
+ * 2 lam ||x||_1), GPL1_STOP_ON_REL_GAP compares that objective with it, and
+ * GPL1_STOP_ON_FW is refused; gpl1_result.f is that objective at the returned x.
+ * PSD keeps the conventions of Alg. GP (x0 projected, f and the stop rules of
+ * eq. 2).  A step that leaves x unchanged stops with GPL1_STOP_STATIONARY. */
+#define GPL1_METHOD_GPSS 0
+#define GPL1_METHOD_ISTA 1
+#define GPL1_METHOD_FISTA 2
+#define GPL1_METHOD_PSD 3
 
 /* gpl1_params.engine.
  *  ONE_READ: one persistent launch of thread-block clusters that reads K once
  *    per iteration.  The gradient is linear in the iterate, so the pass that
  *    forms K x_k and K d_k also forms 2 K^T (K x_k - y) and 2 K^T K d_k from
  *    the same tiles, and g_{k+1} is their combination with the Armijo step
- *    (Alg. GP, Steps 5-6).  GPL1_ERR_UNSUPPORTED when the instance does not fit.
+ *    (Alg. GP, Steps 5-6).  A cluster of C CTAs covers the p columns, each CTA
+ *    a slice of W columns (one 16-byte chunk per thread: W = 2048 F32, 4096
+ *    BF16, 1024 F64; or two chunks, twice that and half the cluster), up to
+ *    C = 16.  ONE_READ lets the autotuner pick the chunks per thread;
+ *    ONE_READ_NCH1 and ONE_READ_NCH2 fix them.  GPL1_ERR_UNSUPPORTED when the
+ *    instance does not fit.
  *  TWO_PASS: one persistent cooperative launch that reads K twice per
- *    iteration (K^T r, then [K d, K x]). */
+ *    iteration (K^T r, then [K d, K x]); p up to 16800 F32/BF16, 3840 F64.
+ *  AUTO: the autotuner picks among all engines that fit.
+ * The autotuner (AUTO, ONE_READ) times each admissible engine the first time
+ * a context meets an instance shape (dtype, n, p): four iterations from
+ * x0 = 0 into a scratch x, twice, on the caller's K and y; the faster wins and
+ * is kept for the context (gpl1_solve_tuned lists the choices).  That first
+ * call synchronises the stream, asynchronous or not. */
 #define GPL1_ENGINE_AUTO 0
 #define GPL1_ENGINE_ONE_READ 1
 #define GPL1_ENGINE_TWO_PASS 2
+#define GPL1_ENGINE_ONE_READ_NCH1 3
+#define GPL1_ENGINE_ONE_READ_NCH2 4
 
 typedef struct {
   int status;          /* gpl1_status of this instance                                 */
@@ -267,6 +304,14 @@ gpl1_status gpl1_gemm_bf16_ex(gpl1_ctx* ctx, const void* A, long long M, long lo
 int gpl1_gemm_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* config, int* splits,
                     float* ms);
 
+/* The single-solve autotuner's choices (gpl1_params.engine AUTO / ONE_READ):
+ * returns the number of tuned shapes (-1 for a NULL ctx); for 0 <= index <
+ * that number it also writes shape[4] = {dtype, n, p, 0 for AUTO or 1 for
+ * ONE_READ}, the engine chosen (GPL1_ENGINE_TWO_PASS, _ONE_READ_NCH1 or
+ * _ONE_READ_NCH2) and its time for the tuning solve (ms).  Any output pointer
+ * may be NULL. */
+int gpl1_solve_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* engine, float* ms);
+
 /* Pins the choice for one product shape (shape[5] = {M, N, Kd, Ka, max_splits},
  * as listed by gpl1_gemm_tuned) in the context's cache, so that the solve uses
  * it without tuning: to reuse choices from an earlier run, or to reproduce a
@@ -294,6 +339,18 @@ gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long long n, long 
                                 const float* Y, long long ldy, const double* rho, const double* f_star,
                                 float* X, long long ldx, int nrhs, const gpl1_params* prm,
                                 gpl1_result* res);
+
+/* ||K||_2^2, the largest eigenvalue of K^T K, by power iteration: `iters`
+ * (1..100000) products with K^T K from a fixed start vector (signs from a
+ * counter-based hash), each an HBM-bound pass of K v and K^T u.  *out (host)
+ * receives the Rayleigh quotient ||K v||^2 of the last unit vector, which never
+ * exceeds ||K||_2^2 and approaches it from below (1/out is then a step s a
+ * little above 1/||K||^2, still inside ISTA's bound of 2/||K||^2).  K (device):
+ * n x p of `dtype`, row stride ldk elements, aligned to its element size.
+ * Uses the context workspace and stream; returns after the result is on the
+ * host. */
+gpl1_status gpl1_spectral_norm_sq(gpl1_ctx* ctx, const void* K, gpl1_dtype dtype, long long n, long long p,
+                                  long long ldk, int iters, double* out);
 
 /* Learned warm start: an unrolled, learned version of the ISTA iteration of
  * Sec. 2 (soft-thresholded Landweber steps),
@@ -326,6 +383,40 @@ gpl1_status gpl1_lista_train(gpl1_ctx* ctx, const void* K, long long n, long lon
                              const float* Y, long long ldy, const float* Xt, long long ldt, long long N,
                              long long batch, int steps, int t0, float lr, float lr_theta,
                              double* losses);
+
+/* The learned warm start as a product.
+ *   gpl1_lista_init: the network's starting point, every layer one ISTA step
+ *     of eq. 1 (Sec. 2) with step 1/L: W_l = K^T / L (device FP32, layers x p
+ *     x n) with L = ||K||_2^2 from gpl1_spectral_norm_sq (`power_iters`
+ *     products), theta_l = lam0 / L (device FP32, layers) with lam0 the median
+ *     of the `count` >= 1 values `lambdas` (host; e.g. gpl1_result.lambda of
+ *     the training solves: the lambda of the lambda-rho relation of Sec. 1);
+ *     *L_out (host, may be NULL) receives L.  K as for gpl1_lista_forward.
+ *   gpl1_solve_warm: nrhs instances of eq. 2 sharing the BF16 K, right-hand
+ *     side b in row b of Y (device FP32, stride ldy), radius rho[b], optimal
+ *     value f_star[b] (host arrays; f_star may be NULL), solution in row b of X
+ *     (device FP32, stride ldx):
+ *       1. x0 = the network's output (gpl1_lista_forward; any nrhs, a ragged
+ *          tail of fewer than 64 rows goes through a zero-padded batch);
+ *       2. Alg. GP + SS from the projection of x0 onto each ball (the shared-K
+ *          form, alpha_0 by rule 1), at most warm_max_iter iterations
+ *          (<= 0: prm->max_iter);
+ *       3. the fallback: every instance whose warm solve did not end with
+ *          GPL1_OK is solved again from x0 = 0 by gpl1_solve with prm, which
+ *          thereby also judges the warm start: a network that does not help
+ *          costs time, never the result.
+ *     res (host, nrhs): the final result of each instance; fell_back (host,
+ *     nrhs ints, may be NULL): 1 where the cold solve ran; *fallbacks (may be
+ *     NULL): how many did.  prm: Alg. GP + SS only.  Uses the context
+ *     workspace, a second buffer for the padded batch, and the stream; returns
+ *     after the results are on the host. */
+gpl1_status gpl1_lista_init(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk, int layers,
+                            const double* lambdas, long long count, int power_iters, float* W, float* theta,
+                            double* L_out);
+gpl1_status gpl1_solve_warm(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk, int layers,
+                            const float* W, const float* theta, const float* Y, long long ldy, const double* rho,
+                            const double* f_star, float* X, long long ldx, int nrhs, const gpl1_params* prm,
+                            int warm_max_iter, gpl1_result* res, int* fell_back, int* fallbacks);
 
 /* ---- Solve without allocating (an addition of this library; the paper has
  * no counterpart).

@@ -24,7 +24,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NOT_CONVERGED", 4: "LINESEAR
 STOP = {0: "rel_gap", 1: "stationary", 2: "fw", 3: "max_iter", 4: "error"}
 STOP_ON_REL_GAP, STOP_ON_FW = 1, 2
 DEBUG_UNREACHABLE_BARRIER = 1
-ENGINE_AUTO, ENGINE_ONE_READ, ENGINE_TWO_PASS = 0, 1, 2
+ENGINE_AUTO, ENGINE_ONE_READ, ENGINE_TWO_PASS, ENGINE_ONE_READ_NCH1, ENGINE_ONE_READ_NCH2 = 0, 1, 2, 3, 4
+METHOD_GPSS, METHOD_ISTA, METHOD_FISTA, METHOD_PSD = 0, 1, 2, 3
 TRACE_COLS = 28
 # statuses that describe how a solve ended (reported in Result.status, not raised)
 ALGORITHMIC = (0, 3, 4, 5, 6)
@@ -33,7 +34,8 @@ EXPORTS = ["gpl1_create", "gpl1_destroy", "gpl1_set_stream", "gpl1_last_error", 
            "gpl1_project", "gpl1_solve", "gpl1_solve_batched", "gpl1_solve_noalloc", "gpl1_gemm_bf16",
            "gpl1_gemm_bf16_ex", "gpl1_gemm_tuned", "gpl1_gemm_tuned_set", "gpl1_solve_shared_k", "gpl1_lista_forward",
            "gpl1_lista_grad", "gpl1_lista_train", "gpl1_plan_create", "gpl1_plan_run", "gpl1_plan_destroy",
-           "gpl1_solve_async", "gpl1_solve_batched_async"]
+           "gpl1_solve_async", "gpl1_solve_batched_async", "gpl1_spectral_norm_sq", "gpl1_lista_init",
+           "gpl1_solve_warm", "gpl1_solve_tuned"]
 
 
 class Gpl1Error(RuntimeError):
@@ -48,7 +50,8 @@ class Params(ctypes.Structure):
                 ("M_alpha", ctypes.c_int), ("tol", ctypes.c_double), ("f_star", ctypes.c_double),
                 ("stop_rule", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_backtracks", ctypes.c_int),
                 ("alpha0_rule", ctypes.c_int), ("x0_is_zero", ctypes.c_int), ("debug", ctypes.c_int),
-                ("timeout_ns", ctypes.c_longlong), ("engine", ctypes.c_int), ("engine_pad", ctypes.c_int)]
+                ("timeout_ns", ctypes.c_longlong), ("engine", ctypes.c_int), ("method", ctypes.c_int),
+                ("lambda_pen", ctypes.c_double), ("step", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -111,6 +114,9 @@ def lib():
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_float)]
         L.gpl1_gemm_tuned.restype = ctypes.c_int
+        L.gpl1_solve_tuned.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+        L.gpl1_solve_tuned.restype = ctypes.c_int
         L.gpl1_gemm_tuned_set.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
                                           ctypes.c_int]
         L.gpl1_solve_shared_k.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
@@ -123,6 +129,11 @@ def lib():
                                       ctypes.POINTER(ctypes.c_double)]
         L.gpl1_lista_train.argtypes = [vp, vp, ll, ll, ll, ci, vp, vp, vp, vp, vp, ll, vp, ll, ll, ll, ci, ci, cf, cf,
                                        vp]
+        L.gpl1_spectral_norm_sq.argtypes = [vp, vp, ci, ll, ll, ll, ci, ctypes.POINTER(ctypes.c_double)]
+        L.gpl1_lista_init.argtypes = [vp, vp, ll, ll, ll, ci, vp, ll, ci, vp, vp, ctypes.POINTER(ctypes.c_double)]
+        L.gpl1_solve_warm.argtypes = [vp, vp, ll, ll, ll, ci, vp, vp, vp, ll, vp, vp, vp, ll, ci,
+                                      ctypes.POINTER(Params), ci, ctypes.POINTER(Result), vp,
+                                      ctypes.POINTER(ctypes.c_int)]
         L.gpl1_solve_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, ctypes.POINTER(Params),
                                          ctypes.POINTER(Result), ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]
         _lib = L
@@ -267,6 +278,18 @@ class Context:
             out.append({"shape": tuple(shp), "config": cfg.value, "splits": spl.value, "ms": ms.value})
         return out
 
+    def solve_tuned(self):
+        """The single-solve autotuner's choices: [{shape: (dtype, n, p, class), engine, ms}]."""
+        L = lib()
+        count = L.gpl1_solve_tuned(self._h, 0, None, None, None)
+        out = []
+        for i in range(max(count, 0)):
+            shp = (ctypes.c_longlong * 4)()
+            eng, ms = ctypes.c_int(), ctypes.c_float()
+            L.gpl1_solve_tuned(self._h, i, shp, ctypes.byref(eng), ctypes.byref(ms))
+            out.append({"shape": tuple(shp), "engine": eng.value, "ms": ms.value})
+        return out
+
     def gemm_tuned_set(self, shape, config, splits):
         """gpl1_gemm_tuned_set: pin (config, splits) for shape (M, N, Kd, Ka, max_splits)."""
         shp = (ctypes.c_longlong * 5)(*[int(v) for v in shape])
@@ -276,6 +299,54 @@ class Context:
     @staticmethod
     def _ptr(t):
         return ctypes.c_void_p(t.data_ptr())
+
+    def spectral_norm_sq(self, K, dtype, p=None, iters=100):
+        """gpl1_spectral_norm_sq: ||K||_2^2 of the n x p matrix K (n x ldk storage)."""
+        n, ldk = K.shape
+        out = ctypes.c_double()
+        self._bind_stream()
+        self._check(lib().gpl1_spectral_norm_sq(self._h, self._ptr(K), int(dtype), n, ldk if p is None else int(p),
+                                                ldk, int(iters), ctypes.byref(out)))
+        return out.value
+
+    def lista_init(self, K, layers, lambdas, p=None, power_iters=100, W=None, theta=None):
+        """gpl1_lista_init: (W (layers, p, n), theta (layers), L) with W_l = K^T / L and
+        theta_l = median(lambdas) / L, L = ||K||_2^2."""
+        import torch
+        n, ldk = K.shape
+        p = ldk if p is None else int(p)
+        W = torch.empty(layers, p, n, dtype=torch.float32, device=K.device) if W is None else W
+        theta = torch.empty(layers, dtype=torch.float32, device=K.device) if theta is None else theta
+        lam = (ctypes.c_double * len(lambdas))(*[float(v) for v in lambdas])
+        L = ctypes.c_double()
+        self._bind_stream()
+        self._check(lib().gpl1_lista_init(self._h, self._ptr(K), n, p, ldk, int(layers), ctypes.cast(lam, ctypes.c_void_p),
+                                          len(lambdas), int(power_iters), self._ptr(W), self._ptr(theta),
+                                          ctypes.byref(L)))
+        return W, theta, L.value
+
+    def solve_warm(self, K, W, theta, Y, rho, f_star=None, params: Params | None = None, warm_max_iter=0, X=None):
+        """gpl1_solve_warm: the network's output as x0 for Alg. GP on every row of Y (nrhs, n),
+        the cold solve as the fallback; returns (X, [Result], fell_back list, fallbacks)."""
+        import torch
+        n, ldk = K.shape
+        layers, p, _ = W.shape
+        nrhs = Y.shape[0]
+        X = torch.empty(nrhs, p, dtype=torch.float32, device=K.device) if X is None else X
+        _same_device(self.device, K, W, theta, Y, X)
+        prm = params_default() if params is None else params
+        rho_h = (ctypes.c_double * nrhs)(*[float(r) for r in rho])
+        fs_h = None if f_star is None else (ctypes.c_double * nrhs)(*[float(f) for f in f_star])
+        res = (Result * nrhs)()
+        fb = (ctypes.c_int * nrhs)()
+        nfb = ctypes.c_int()
+        self._bind_stream()
+        self._check(lib().gpl1_solve_warm(self._h, self._ptr(K), n, p, ldk, layers, self._ptr(W), self._ptr(theta),
+                                          self._ptr(Y), Y.stride(0), ctypes.cast(rho_h, ctypes.c_void_p),
+                                          None if fs_h is None else ctypes.cast(fs_h, ctypes.c_void_p), self._ptr(X),
+                                          X.stride(0), nrhs, ctypes.byref(prm), int(warm_max_iter), res,
+                                          ctypes.cast(fb, ctypes.c_void_p), ctypes.byref(nfb)))
+        return X, list(res), list(fb), nfb.value
 
     def lista_forward(self, K, W, theta, Y, p=None, X=None):
         """gpl1_lista_forward: x^L (B, p) float32 for right-hand sides Y (B, n)."""

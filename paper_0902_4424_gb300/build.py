@@ -16,7 +16,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libgpl1.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["api.cu", "project.cu", "gpss_f64.cu", "gpss_f32.cu", "gpss_bf16.cu", "gemm_tc.cu", "shared_k.cu",
+SOURCES = ["api.cu", "power.cu", "project.cu", "gpss_f64.cu", "gpss_f32.cu", "gpss_bf16.cu", "gemm_tc.cu", "shared_k.cu",
            "lista.cu", "autotune.cu", "fused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]

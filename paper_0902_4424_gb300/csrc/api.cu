@@ -33,6 +33,10 @@ struct gpl1_ctx {
   std::map<std::vector<long long>, gpl1::GemmChoice> gemm_tuned;
   // one-read kernel: resident clusters per (dtype, chunks per thread, cluster size)
   std::map<std::vector<int>, int> fused_resident;
+  void* aux = nullptr;              // second device buffer (the warm-start call's padded rows)
+  size_t aux_bytes = 0;
+  // single-solve autotuner: (dtype, n, p, engine class) -> engine and tuned ms
+  std::map<std::vector<long long>, std::pair<int, float>> solve_tuned;
 };
 
 namespace {
@@ -77,6 +81,20 @@ gpl1_status ensure_ws(gpl1_ctx* ctx, size_t bytes) {
   return GPL1_OK;
 }
 
+// A second device buffer of the context (scratch that must not share the workspace).
+gpl1_status ensure_aux(gpl1_ctx* ctx, size_t bytes) {
+  if (ctx->aux_bytes >= bytes) return GPL1_OK;
+  if (ctx->aux) {
+    GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    cudaFree(ctx->aux);
+    ctx->aux = nullptr;
+    ctx->aux_bytes = 0;
+  }
+  GPL1_CUDA(cudaMalloc(&ctx->aux, bytes), "cudaMalloc(aux)");
+  ctx->aux_bytes = bytes;
+  return GPL1_OK;
+}
+
 gpl1_status ensure_host_res(gpl1_ctx* ctx, size_t count) {
   if (count <= ctx->host_res_count) return GPL1_OK;
   if (ctx->host_res) cudaFreeHost(ctx->host_res);
@@ -86,8 +104,25 @@ gpl1_status ensure_host_res(gpl1_ctx* ctx, size_t count) {
   return GPL1_OK;
 }
 
-gpl1_status check_params(gpl1_ctx* ctx, const gpl1_params* p) {
+// methods: whether the caller runs the comparison methods of Sec. 2 (single
+// solves on the one-read kernel); every other entry point runs Alg. GP + SS only.
+gpl1_status check_params(gpl1_ctx* ctx, const gpl1_params* p, bool methods = false) {
   if (!p) return fail(ctx, GPL1_ERR_INVALID_ARG, "params is NULL");
+  if (p->method < GPL1_METHOD_GPSS || p->method > GPL1_METHOD_PSD)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "method must be GPL1_METHOD_GPSS, _ISTA, _FISTA or _PSD");
+  if (p->method != GPL1_METHOD_GPSS) {
+    if (!methods)
+      return fail(ctx, GPL1_ERR_UNSUPPORTED, "ISTA, FISTA and PSD run in gpl1_solve and gpl1_solve_async only");
+    if (p->engine == GPL1_ENGINE_TWO_PASS)
+      return fail(ctx, GPL1_ERR_UNSUPPORTED, "ISTA, FISTA and PSD run on the one-read engine only");
+    const bool eq1 = p->method == GPL1_METHOD_ISTA || p->method == GPL1_METHOD_FISTA;
+    if (eq1 && (!(p->lambda_pen > 0) || !std::isfinite(p->lambda_pen)))
+      return fail(ctx, GPL1_ERR_INVALID_ARG, "ISTA and FISTA need a finite lambda_pen > 0");
+    if (eq1 && (!(p->step > 0) || !std::isfinite(p->step)))
+      return fail(ctx, GPL1_ERR_INVALID_ARG, "ISTA and FISTA need a finite step > 0");
+    if (eq1 && (p->stop_rule & GPL1_STOP_ON_FW))
+      return fail(ctx, GPL1_ERR_INVALID_ARG, "GPL1_STOP_ON_FW is a certificate of eq. 2, not of ISTA/FISTA's eq. 1");
+  }
   if (!(p->beta > 0 && p->beta < 1) || !(p->theta > 0 && p->theta < 1))
     return fail(ctx, GPL1_ERR_INVALID_ARG, "beta and theta must lie in (0,1)");
   if (p->M < 1 || p->M > kMaxM) return fail(ctx, GPL1_ERR_INVALID_ARG, "M must lie in [1,%d]", kMaxM);
@@ -100,8 +135,8 @@ gpl1_status check_params(gpl1_ctx* ctx, const gpl1_params* p) {
   if (p->max_iter < 1 || p->max_backtracks < 0) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad max_iter/max_backtracks");
   if (p->timeout_ns <= 0) return fail(ctx, GPL1_ERR_INVALID_ARG, "timeout_ns must be > 0");
   if (p->alpha0_rule != 0 && p->alpha0_rule != 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "alpha0_rule is 0 or 1");
-  if (p->engine < GPL1_ENGINE_AUTO || p->engine > GPL1_ENGINE_TWO_PASS)
-    return fail(ctx, GPL1_ERR_INVALID_ARG, "engine must be GPL1_ENGINE_AUTO, _ONE_READ or _TWO_PASS");
+  if (p->engine < GPL1_ENGINE_AUTO || p->engine > GPL1_ENGINE_ONE_READ_NCH2)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "engine must be one of GPL1_ENGINE_*");
   return GPL1_OK;
 }
 
@@ -169,6 +204,10 @@ SolveParams to_kernel_params(const gpl1_params* p) {
   s.alpha0_rule = p->alpha0_rule;
   s.timeout_ns = p->timeout_ns;
   s.debug = p->debug;
+  s.method = p->method;
+  s.method_pad = 0;
+  s.lam_pen = p->lambda_pen;
+  s.step = p->step;
   return s;
 }
 
@@ -209,6 +248,9 @@ void gpl1_params_default(gpl1_params* p) {
   p->alpha0_rule = 0;
   p->x0_is_zero = 0;
   p->timeout_ns = 10LL * 1000 * 1000 * 1000;
+  p->method = GPL1_METHOD_GPSS;
+  p->lambda_pen = 0.0;
+  p->step = 1.0;
 }
 
 gpl1_status gpl1_create(gpl1_ctx** out, int device, void* stream) {
@@ -235,6 +277,7 @@ void gpl1_destroy(gpl1_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->ws);
   }
+  if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->host_res) cudaFreeHost(ctx->host_res);
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
@@ -481,10 +524,19 @@ struct OneRead {
 // Chunks per thread and cluster size for p columns (the smallest cluster that
 // covers p with one chunk per thread, else with two; portable sizes first),
 // and the number of clusters that stay resident together.
-gpl1_status one_read_choose(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, OneRead* o) {
+gpl1_status one_read_choose(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, OneRead* o, int want_nch = 0) {
   const long long p = pr->p;
   int nch = 0, C = 0;
+  if (want_nch) {   // a given number of chunks per thread (the autotuner's candidates)
+    const long long w = fused_width(dt, want_nch);
+    const long long c = (p + w - 1) / w;
+    if (c > fz::kCMax)
+      return fail(ctx, GPL1_ERR_UNSUPPORTED, "p = %lld needs clusters of more than %d CTAs", p, fz::kCMax);
+    nch = want_nch;
+    C = static_cast<int>(c);
+  }
   for (int cand : {1, 2}) {
+    if (nch) break;
     const long long w = fused_width(dt, cand);
     const long long c = (p + w - 1) / w;
     if (c <= 8) {
@@ -577,8 +629,59 @@ gpl1_status one_read_enqueue(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, cons
   return GPL1_OK;
 }
 
-// Which engine runs this single solve (GPL1_OK with *use_one_read set, or an
-// error for GPL1_ENGINE_ONE_READ on an instance it cannot take).
+gpl1_status run_one_read(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl1_params* prm, const OneRead& o,
+                         gpl1_result* res, gpl1_result* res_dev);
+
+constexpr int kTuneIters = 4;   // Alg. GP iterations of a timed candidate solve
+
+// The autotuner of the single solve: each admissible engine (the one-read
+// kernel with one or two column chunks per thread, which changes the cluster
+// size and the rows per block, and, for GPL1_ENGINE_AUTO, the two-pass
+// kernel) solves the instance for kTuneIters iterations from x0 = 0 into a
+// scratch x, twice; the faster second run wins, per (dtype, n, p, engine
+// class) and context.
+gpl1_status tune_engine(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl1_params* prm,
+                        const std::vector<int>& cands, int* best) {
+  const size_t vs = dt == GPL1_F64 ? 8 : 4;
+  gpl1_status st = ensure_aux(ctx, static_cast<size_t>(pr->p) * vs + 256);
+  if (st) return st;
+  gpl1_problem tp = *pr;
+  tp.x = ctx->aux;
+  tp.trace = nullptr;
+  tp.trace_cap = 0;
+  gpl1_params tq = *prm;
+  tq.stop_rule = 0;
+  tq.max_iter = kTuneIters;
+  tq.x0_is_zero = 1;
+  float best_ms = 0.f;
+  *best = -1;
+  for (int eng : cands) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      gpl1_result r;
+      if (eng == GPL1_ENGINE_TWO_PASS) {
+        st = run(ctx, &tp, 1, dt, &tq, &r);
+      } else {
+        OneRead o;
+        if ((st = one_read_choose(ctx, &tp, dt, &o, eng == GPL1_ENGINE_ONE_READ_NCH2 ? 2 : 1))) return st;
+        st = run_one_read(ctx, &tp, dt, &tq, o, &r, nullptr);
+      }
+      if (st != GPL1_OK && st != GPL1_ERR_NOT_CONVERGED && st != GPL1_ERR_LINESEARCH) return st;
+      ms = static_cast<float>(r.kernel_ms);
+    }
+    if (*best < 0 || ms < best_ms) {
+      *best = eng;
+      best_ms = ms;
+    }
+  }
+  const std::vector<long long> key = {dt, pr->n, pr->p, prm->engine == GPL1_ENGINE_AUTO ? 0 : 1};
+  ctx->solve_tuned[key] = {*best, best_ms};
+  return GPL1_OK;
+}
+
+// Which engine runs this single solve (GPL1_OK with *use_one_read set and *o
+// filled for the one-read kernel, or an error when the engine asked for cannot
+// take the instance).
 gpl1_status pick_engine(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl1_params* prm, OneRead* o,
                         bool* use_one_read) {
   *use_one_read = false;
@@ -587,13 +690,38 @@ gpl1_status pick_engine(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl
   if (st) return st;
   if (pr->n > (1LL << 30) || pr->p > (1LL << 30)) return fail(ctx, GPL1_ERR_UNSUPPORTED, "n or p too large");
   GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-  st = one_read_choose(ctx, pr, dt, o);
-  if (st == GPL1_OK) {
+  if (prm->engine == GPL1_ENGINE_ONE_READ_NCH1 || prm->engine == GPL1_ENGINE_ONE_READ_NCH2) {
+    if ((st = one_read_choose(ctx, pr, dt, o, prm->engine == GPL1_ENGINE_ONE_READ_NCH2 ? 2 : 1))) return st;
     *use_one_read = true;
     return GPL1_OK;
   }
-  if (prm->engine == GPL1_ENGINE_ONE_READ) return st;
-  return check_problem(ctx, pr, dt, 0, true);   // the two-pass kernel's own limits
+  // the admissible candidates
+  std::vector<int> cands;
+  gpl1_status last = GPL1_OK;
+  for (int nch : {1, 2}) {
+    OneRead t;
+    const gpl1_status s1 = one_read_choose(ctx, pr, dt, &t, nch);
+    if (s1 == GPL1_OK) cands.push_back(nch == 1 ? GPL1_ENGINE_ONE_READ_NCH1 : GPL1_ENGINE_ONE_READ_NCH2);
+    else last = s1;
+  }
+  const bool two_ok = prm->engine == GPL1_ENGINE_AUTO && prm->method == GPL1_METHOD_GPSS &&
+                      pr->p <= static_cast<long long>(gpss_vmax(dt)) * kConsumers;
+  if (two_ok) cands.push_back(GPL1_ENGINE_TWO_PASS);
+  if (cands.empty()) return last ? last : check_problem(ctx, pr, dt, 0, true);
+  int eng = cands[0];
+  if (cands.size() > 1) {
+    const std::vector<long long> key = {dt, pr->n, pr->p, prm->engine == GPL1_ENGINE_AUTO ? 0 : 1};
+    auto it = ctx->solve_tuned.find(key);
+    if (it != ctx->solve_tuned.end()) {
+      eng = it->second.first;
+    } else if ((st = tune_engine(ctx, pr, dt, prm, cands, &eng))) {
+      return st;
+    }
+  }
+  if (eng == GPL1_ENGINE_TWO_PASS) return check_problem(ctx, pr, dt, 0, true);
+  if ((st = one_read_choose(ctx, pr, dt, o, eng == GPL1_ENGINE_ONE_READ_NCH2 ? 2 : 1))) return st;
+  *use_one_read = true;
+  return GPL1_OK;
 }
 
 gpl1_status run_one_read(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl1_params* prm, const OneRead& o,
@@ -625,7 +753,7 @@ gpl1_status gpl1_solve(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype dt, c
   if (!ctx) return GPL1_ERR_INVALID_ARG;
   if (dt != GPL1_F64 && dt != GPL1_F32 && dt != GPL1_BF16) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad dtype");
   if (!res) return fail(ctx, GPL1_ERR_INVALID_ARG, "result is NULL");
-  gpl1_status st = check_params(ctx, prm);
+  gpl1_status st = check_params(ctx, prm, true);
   if (st) return st;
   OneRead o;
   bool one = false;
@@ -640,7 +768,7 @@ gpl1_status gpl1_solve_async(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype
   if (!ctx) return GPL1_ERR_INVALID_ARG;
   if (dt != GPL1_F64 && dt != GPL1_F32 && dt != GPL1_BF16) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad dtype");
   if (!res_dev) return fail(ctx, GPL1_ERR_INVALID_ARG, "result is NULL");
-  gpl1_status st = check_params(ctx, prm);
+  gpl1_status st = check_params(ctx, prm, true);
   if (st) return st;
   OneRead o;
   bool one = false;
@@ -1008,6 +1136,19 @@ extern "C" gpl1_status gpl1_gemm_tuned_set(gpl1_ctx* ctx, const long long* shape
   return GPL1_OK;
 }
 
+extern "C" int gpl1_solve_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* engine, float* ms) {
+  if (!ctx) return -1;
+  const int count = static_cast<int>(ctx->solve_tuned.size());
+  if (index < 0 || index >= count) return count;
+  auto it = ctx->solve_tuned.begin();
+  std::advance(it, index);
+  if (shape)
+    for (int q = 0; q < 4; ++q) shape[q] = it->first[q];
+  if (engine) *engine = it->second.first;
+  if (ms) *ms = it->second.second;
+  return count;
+}
+
 extern "C" int gpl1_gemm_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* config, int* splits,
                                float* ms) {
   if (!ctx) return -1;
@@ -1228,6 +1369,27 @@ gpl1_status lista_status(gpl1_ctx* ctx, int r, int* gerr) {
 
 }  // namespace
 
+// gpl1_spectral_norm_sq: power iteration on K^T K (power.cu).
+extern "C" gpl1_status gpl1_spectral_norm_sq(gpl1_ctx* ctx, const void* K, gpl1_dtype dt, long long n, long long p,
+                                             long long ldk, int iters, double* out) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  if (dt != GPL1_F64 && dt != GPL1_F32 && dt != GPL1_BF16) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad dtype");
+  if (!K || !out) return fail(ctx, GPL1_ERR_INVALID_ARG, "K and out must not be NULL");
+  if (n < 1 || p < 1 || ldk < p) return fail(ctx, GPL1_ERR_INVALID_ARG, "need n, p >= 1 and ldk >= p");
+  if (n > (1LL << 30) || p > (1LL << 30)) return fail(ctx, GPL1_ERR_UNSUPPORTED, "n or p too large");
+  if (iters < 1 || iters > 100000) return fail(ctx, GPL1_ERR_INVALID_ARG, "iters must lie in [1, 100000]");
+  if (reinterpret_cast<uintptr_t>(K) % elem_size(dt) != 0)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "K must be aligned to its element size");
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  gpl1_status st = ensure_ws(ctx, power_ws_bytes(n, p, iters));
+  if (st) return st;
+  GPL1_CUDA(launch_power(dt, K, ldk, static_cast<int>(n), static_cast<int>(p), iters, ctx->ws, out, ctx->stream),
+            "power iteration");
+  GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "power iteration");
+  if (!std::isfinite(*out)) return fail(ctx, GPL1_ERR_NONFINITE, "power iteration: non-finite estimate");
+  return GPL1_OK;
+}
+
 extern "C" gpl1_status gpl1_lista_forward(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
                                           int layers, const float* W, const float* theta, const float* Y,
                                           long long ldy, long long B, float* X, long long ldx) {
@@ -1307,4 +1469,145 @@ extern "C" gpl1_status gpl1_lista_train(gpl1_ctx* ctx, const void* K, long long 
     GPL1_CUDA(cudaMemcpyAsync(losses, dloss, static_cast<size_t>(steps) * 8, cudaMemcpyDeviceToHost, ctx->stream),
               "cudaMemcpyAsync");
   return lista_status(ctx, 0, gerr);
+}
+
+// ---------------------------------------------------------------------------
+// The learned warm start as a product: the network's initial weights, and
+// warm-started solves with the plain cold solve as the fallback.
+
+namespace {
+
+bool solver_outcome(gpl1_status st) {
+  return st == GPL1_OK || st == GPL1_ERR_NOT_CONVERGED || st == GPL1_ERR_LINESEARCH || st == GPL1_ERR_NONFINITE ||
+         st == GPL1_ERR_TIMEOUT;
+}
+
+constexpr long long kWarmChunk = 4096;   // right-hand sides per network pass and per shared-K call
+
+// x^L of rows [b0, b0 + m) of Y into the same rows of X: whole batches of 64
+// directly, a ragged tail through a zero-padded 64-row buffer.
+gpl1_status warm_forward(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk, int layers,
+                         const float* W, const float* theta, const float* Y, long long ldy, float* X, long long ldx,
+                         long long b0, long long m) {
+  const long long full = m / 64 * 64;
+  gpl1_status st;
+  if (full > 0) {
+    if ((st = ensure_ws(ctx, 256 + lista_ws_bytes(layers, n, p, full)))) return st;
+    uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
+    int* gerr = reinterpret_cast<int*>(ws);
+    GPL1_CUDA(cudaMemsetAsync(gerr, 0, sizeof(int), ctx->stream), "cudaMemsetAsync");
+    const int r = lista_pass(ctx->encode, ws + 256, gerr, K, n, p, ldk, layers, W, true, theta, Y + b0 * ldy, ldy,
+                             full, nullptr, 0, X + b0 * ldx, ldx, nullptr, nullptr, nullptr, ctx->stream);
+    if ((st = lista_status(ctx, r, gerr))) return st;
+  }
+  const long long t = m - full;
+  if (t == 0) return GPL1_OK;
+  if ((st = ensure_aux(ctx, static_cast<size_t>(64) * (n + p) * sizeof(float)))) return st;
+  float* Yp = static_cast<float*>(ctx->aux);
+  float* Xp = Yp + 64 * n;
+  GPL1_CUDA(cudaMemsetAsync(Yp, 0, static_cast<size_t>(64) * n * sizeof(float), ctx->stream), "cudaMemsetAsync");
+  GPL1_CUDA(cudaMemcpy2DAsync(Yp, n * sizeof(float), Y + (b0 + full) * ldy, ldy * sizeof(float), n * sizeof(float),
+                              t, cudaMemcpyDeviceToDevice, ctx->stream),
+            "cudaMemcpy2DAsync");
+  if ((st = ensure_ws(ctx, 256 + lista_ws_bytes(layers, n, p, 64)))) return st;
+  uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
+  int* gerr = reinterpret_cast<int*>(ws);
+  GPL1_CUDA(cudaMemsetAsync(gerr, 0, sizeof(int), ctx->stream), "cudaMemsetAsync");
+  const int r = lista_pass(ctx->encode, ws + 256, gerr, K, n, p, ldk, layers, W, true, theta, Yp, n, 64, nullptr, 0,
+                           Xp, p, nullptr, nullptr, nullptr, ctx->stream);
+  if ((st = lista_status(ctx, r, gerr))) return st;
+  GPL1_CUDA(cudaMemcpy2DAsync(X + (b0 + full) * ldx, ldx * sizeof(float), Xp, p * sizeof(float), p * sizeof(float), t,
+                              cudaMemcpyDeviceToDevice, ctx->stream),
+            "cudaMemcpy2DAsync");
+  return GPL1_OK;
+}
+
+}  // namespace
+
+extern "C" gpl1_status gpl1_lista_init(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
+                                       int layers, const double* lambdas, long long count, int power_iters, float* W,
+                                       float* theta, double* L_out) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  gpl1_status st = check_lista(ctx, K, n, p, ldk, layers, 64);
+  if (st) return st;
+  if (!W || !theta || !lambdas || count < 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "need W, theta and lambdas");
+  std::vector<double> lam(lambdas, lambdas + count);
+  for (double v : lam)
+    if (!(v >= 0) || !std::isfinite(v)) return fail(ctx, GPL1_ERR_INVALID_ARG, "lambdas must be finite, >= 0");
+  double L = 0.0;
+  if ((st = gpl1_spectral_norm_sq(ctx, K, GPL1_BF16, n, p, ldk, power_iters, &L))) return st;
+  if (!(L > 0)) return fail(ctx, GPL1_ERR_INVALID_ARG, "K is zero");
+  // the median of the lambdas (the mean of the two middle values for an even count)
+  std::sort(lam.begin(), lam.end());
+  const size_t c = lam.size();
+  const double med = c % 2 ? lam[c / 2] : 0.5 * (lam[c / 2 - 1] + lam[c / 2]);
+  GPL1_CUDA(lista_init_weights(K, ldk, static_cast<int>(n), static_cast<int>(p), layers, static_cast<float>(1.0 / L), W,
+                               ctx->stream),
+            "network initialisation");
+  std::vector<float> th(static_cast<size_t>(layers), static_cast<float>(med / L));
+  GPL1_CUDA(cudaMemcpyAsync(theta, th.data(), th.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream),
+            "cudaMemcpyAsync(theta)");
+  GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "network initialisation");
+  if (L_out) *L_out = L;
+  return GPL1_OK;
+}
+
+extern "C" gpl1_status gpl1_solve_warm(gpl1_ctx* ctx, const void* K, long long n, long long p, long long ldk,
+                                       int layers, const float* W, const float* theta, const float* Y, long long ldy,
+                                       const double* rho, const double* f_star, float* X, long long ldx, int nrhs,
+                                       const gpl1_params* prm, int warm_max_iter, gpl1_result* res, int* fell_back,
+                                       int* fallbacks) {
+  if (!ctx) return GPL1_ERR_INVALID_ARG;
+  if (!W || !theta || !Y || !rho || !X || !res || nrhs < 1 || ldy < n || ldx < p)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "NULL pointer, nrhs < 1 or bad stride");
+  gpl1_status st = check_params(ctx, prm);
+  if (st) return st;
+  if ((st = check_lista(ctx, K, n, p, ldk, layers, 64))) return st;
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if ((st = ensure_encode(ctx))) return st;
+  // 1. the network's output for every right-hand side (the warm start x0)
+  for (long long b0 = 0; b0 < nrhs; b0 += kWarmChunk)
+    if ((st = warm_forward(ctx, K, n, p, ldk, layers, W, theta, Y, ldy, X, ldx, b0,
+                           std::min<long long>(kWarmChunk, nrhs - b0))))
+      return st;
+  // 2. Alg. GP + SS from its projection onto each ball (shared-K form; alpha_0
+  //    from the projected-gradient step at x0, rule 1)
+  gpl1_params pw = *prm;
+  pw.x0_is_zero = 0;
+  pw.alpha0_rule = 1;
+  if (warm_max_iter > 0) pw.max_iter = warm_max_iter;
+  for (long long b0 = 0; b0 < nrhs; b0 += kWarmChunk) {
+    const int m = static_cast<int>(std::min<long long>(kWarmChunk, nrhs - b0));
+    st = gpl1_solve_shared_k(ctx, K, n, p, ldk, Y + b0 * ldy, ldy, rho + b0, f_star ? f_star + b0 : nullptr,
+                             X + b0 * ldx, ldx, m, &pw, res + b0);
+    if (!solver_outcome(st)) return st;
+  }
+  // 3. the fallback: every instance the warm solve did not bring to the stop is
+  //    solved again from x0 = 0 by the plain solver with the caller's parameters
+  gpl1_params pc = *prm;
+  pc.x0_is_zero = 1;
+  pc.engine = GPL1_ENGINE_AUTO;
+  int nfb = 0;
+  for (int b = 0; b < nrhs; ++b) {
+    if (fell_back) fell_back[b] = 0;
+    if (res[b].status == GPL1_OK) continue;
+    gpl1_problem pr;
+    std::memset(&pr, 0, sizeof pr);
+    pr.K = K;
+    pr.n = n;
+    pr.p = p;
+    pr.ldk = ldk;
+    pr.y = Y + b * ldy;
+    pr.rho = rho[b];
+    pr.x = X + b * ldx;
+    pr.f_star = f_star ? f_star[b] : -1.0;
+    gpl1_result r;
+    st = gpl1_solve(ctx, &pr, GPL1_BF16, &pc, &r);
+    if (!solver_outcome(st)) return st;
+    res[b] = r;
+    if (fell_back) fell_back[b] = 1;
+    ++nfb;
+  }
+  if (fallbacks) *fallbacks = nfb;
+  return GPL1_OK;
 }

@@ -332,6 +332,11 @@ struct FState {
   int stop, iters, backtracks, inside, status, done, acc, nz;
   int tau_steps;
   unsigned long long ts[10];
+  // comparison methods (Sec. 2): objective of the method's problem at x_k,
+  // ||g_k||^2 and ||K g_k||^2 (PSD), and the coefficient of U2 in the next
+  // gradient (1 after a pass along x_{k+1} - x_k, 0 after the setup or a probe)
+  double F_cur, gg, kb2p;
+  int cpass;
 };
 
 template <int DT, int NCH>
@@ -453,12 +458,15 @@ struct FC {
   const unsigned rank, cid;
   const int C, NC, G, cta, n, p;
   int bk0, bk1;
-  uint32_t ita = 0, itb = 0, rseq = 0, sseq = 0;
+  uint32_t rseq = 0, sseq = 0;
+  // stage and phase of the next block of each ring (A: from HBM, B: from L2)
+  uint32_t sta = 0, pha = 0, stb = 0, phb = 0;
   unsigned epoch = 0;
   int bsl = 0;
   int status = GPL1_OK;
 
   A x[NE], d[NE], g[NE], u1[NE], u2[NE];
+  double tk = 1.0;  // FISTA's t_k (every thread keeps the same sequence)
   bool cv[NCH];
   int gcol[NCH];    // global column of the chunk's first element
   int soff[NCH];    // byte offset of the chunk in row 0 of a stage
@@ -505,6 +513,8 @@ struct FC {
   // spin: poll without sleeping (for the waits on the critical path of the
   // row-sum exchange, where the wake-up of a suspended warp would add latency)
   __device__ bool wwait(uint64_t* bar, uint32_t par, int site, bool cl, bool spin = false) {
+    // fast path: the phase is already complete; every lane takes it itself
+    if (__all_sync(0xffffffffu, poll(bar, par, cl, spin))) return true;
     int ok = 1;
     if (lane == 0) {
       if (failed()) {
@@ -1089,12 +1099,15 @@ struct FC {
         // ---- step A: block j of chunk c (from HBM): its row sums
         if (hasA) {
           if (j < cntA) {
-            const uint32_t st = ita % kNSA;
-            const bool ok = wwait(&sm.full[st], (ita / kNSA) & 1u, kSitePassA, false);
+            const uint32_t st = sta;
+            const bool ok = wwait(&sm.full[st], pha, kSitePassA, false);
             if (dots && ok) row_partials<ACC>(sm.stage[st], &sm.red[s3][warp][RWPR * R * j]);
             __syncwarp();
             if (lane == 0 && ok) mbar_arrive(&sm.empty[st]);
-            ++ita;
+            if (++sta == kNSA) {
+              sta = 0;
+              pha ^= 1u;
+            }
           } else if (dots) {   // past the last block of the pass
             if (lane < RWPR * R) sm.red[s3][warp][RWPR * R * j + lane] = 0u;
           }
@@ -1130,8 +1143,8 @@ struct FC {
               m2[qq] = A(0);
             }
           }
-          const uint32_t st = kNSA + itb % kNSB;
-          const bool ok = wwait(&sm.full[st], (itb / kNSB) & 1u, kSitePassB, false);
+          const uint32_t st = kNSA + stb;
+          const bool ok = wwait(&sm.full[st], phb, kSitePassB, false);
           if (ok && okt) {
             const uint8_t* stg = sm.stage[st];
 #pragma unroll
@@ -1151,7 +1164,10 @@ struct FC {
           }
           __syncwarp();
           if (lane == 0 && ok) mbar_arrive(&sm.empty[st]);
-          ++itb;
+          if (++stb == kNSB) {
+            stb = 0;
+            phb ^= 1u;
+          }
         }
       }
       if (hasA && dots) {
@@ -1819,6 +1835,313 @@ struct FC {
     csync();
   }
 
+  // ---------------------------------------------------- comparison methods
+  // ISTA, FISTA and PSD (Sec. 2) on the same passes.  After pass s the
+  // gradient at x_k is g_k = U1 + c U2 with c = cpass.  FISTA evaluates the
+  // gradient at z_k = x_k + w_k (x_k - x_{k-1}) instead, and since the pass
+  // carried d_{k-1} = x_k - x_{k-1}, g(z_k) = g_k + w_k U2 (the gradient is
+  // linear in the point).  mode 0: ISTA / FISTA step, d_k = S(v) - x_k with
+  // v = z_k - (s/2) g(z_k) (= z_k + s K^T (y - K z_k)); mode 1: PSD probe, the
+  // pass's direction is g_k (its ||K g_k||^2 gives beta_k); mode 2: PSD step,
+  // d_k = P(x_k - (beta_k/2) g_k) - x_k (= P(x_k + beta_k r_k) - x_k).
+  // Modes 0 and 1 open iteration k with its stop tests at x_k.  Returns false
+  // when the solve stops here (x_k is the answer) or failed.
+  __device__ bool phase_m(int k, int s, int mode) {
+    FState& u = sm.st;
+    const SolveParams& P = a.prm;
+    const bool eq1 = P.method != GPL1_METHOD_PSD;
+    const A* const U1 = static_cast<const A*>(a.U) + static_cast<long long>(s % 3) * 2 * a.pp;
+    const A* const U2 = U1 + a.pp;
+    const A c = u.cpass ? A(1) : A(0);
+    double wk = 0.0;
+    if (mode == 0 && P.method == GPL1_METHOD_FISTA) {
+      const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+      wk = (tk - 1.0) / tn;
+      tk = tn;
+    }
+    const A w = static_cast<A>(wk);
+    A gz[NE];
+    A gg = 0, gm = 0;
+    S gx{}, l1{};
+#pragma unroll
+    for (int m = 0; m < NCH; ++m) {
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) {
+        const int j = m * EPC + e;
+        gz[j] = A(0);
+        if (!cv[m]) continue;
+        const A v2 = ldg_cg(U2 + gcol[m] + e);
+        const A gn = vfma(c, v2, ldg_cg(U1 + gcol[m] + e));
+        g[j] = gn;
+        gz[j] = vfma(w, v2, gn);
+        gg = vfma(gn, gn, gg);
+        acc_mul(gx, gn, x[j]);
+        gm = vmax(gm, vabs(gn));
+        if constexpr (!kF64) l1 = f2_add(l1, fabsf(x[j]));
+        else l1 += fabs(x[j]);
+      }
+    }
+    {   // clear this CTA's share of the buffer the pass after next adds into
+      A* const Z = static_cast<A*>(a.U) + static_cast<long long>((s + 2) % 3) * 2 * a.pp;
+      const long long tot = 2 * a.pp, j0 = tot * cta / G, j1 = tot * (cta + 1) / G;
+      for (long long j = j0 + tid; j < j1; j += kCons) Z[j] = A(0);
+    }
+    using CbP = Comb<S, 3, 1, 0, kF64>;
+    uint32_t wr[CbP::NW];
+    if constexpr (!kF64) put(wr, F2{gg, 0.f});
+    else put(wr, gg);
+    put(wr + 2, gx);
+    put(wr + 4, l1);
+    put_max(wr + 6, gm);
+    reduce<CbP>(wr, true);
+    if (tid == 0) {
+      double ggd, gxd, l1d;
+      if constexpr (!kF64) {
+        ggd = as_double(get_f2(wr));
+        gxd = as_double(get_f2(wr + 2));
+        const F2 l1p = get_f2(wr + 4);
+        l1d = as_double(l1p);
+        u.gmaxf = get_max_f(wr + 6);
+        u.gmax = static_cast<double>(u.gmaxf);
+        // PSD iterates lie in the ball: rounding in x + d can leave ||x||_1 a
+        // few ulps above rho, and the iterate is scaled back (as in Alg. GP)
+        const float ex = (l1p.hi - u.rho_p.hi) + (l1p.lo - u.rho_p.lo);
+        u.xscale = (!eq1 && mode == 1 && ex > 0.f) ? __fdiv_rd(u.rho_p.hi, l1p.hi) * (1.f - 0x1p-21f) : 1.f;
+      } else {
+        ggd = get_d(wr);
+        gxd = get_d(wr + 2);
+        l1d = get_d(wr + 4);
+        u.gmax = get_max_d(wr + 6);
+        u.gmaxf = static_cast<float>(u.gmax) * 1.0000002f;
+        u.xscale = 1.f;
+        u.xscale_d = (!eq1 && mode == 1 && l1d > a.rho) ? (a.rho / l1d) * (1.0 - 0x1p-50) : 1.0;
+      }
+      u.gx = gxd;
+      if (mode != 2) {   // stop tests at x_k: the objective of the method's problem
+        const double obj = eq1 ? u.f_cur + 2.0 * P.lam_pen * l1d : u.f_cur;
+        u.F_cur = obj;
+        if ((P.stop_rule & GPL1_STOP_ON_REL_GAP) && a.f_star >= 0.0) {
+          if (obj - a.f_star <= kAccGapFactor * P.tol * u.gap_den) u.acc = 1;
+          if (obj - a.f_star <= P.tol * u.gap_den) {
+            u.stop = GPL1_STOP_REL_GAP;
+            u.iters = k;
+            u.done = 1;
+          }
+        }
+        if (!eq1 && !u.done && (P.stop_rule & GPL1_STOP_ON_FW)) {
+          const double fw = gxd + a.rho * u.gmax;
+          if (fw <= kAccGapFactor * P.tol * (u.f_cur - fw)) u.acc = 1;
+          if (fw <= P.tol * (u.f_cur - fw)) {
+            u.stop = GPL1_STOP_FW;
+            u.iters = k;
+            u.done = 1;
+          }
+        }
+        if (!isfinite(obj) && !u.done) {
+          u.status = GPL1_ERR_NONFINITE;
+          u.stop = GPL1_STOP_ERROR;
+          u.iters = k;
+          u.done = 1;
+        }
+      }
+      if (!u.done) {
+        if (eq1) {
+          u.alpha = 0.5 * P.step;
+          u.ah = static_cast<float>(u.alpha);
+          u.tau64 = P.step * P.lam_pen;
+          u.th = static_cast<float>(u.tau64);
+          u.tl = 0.f;
+        } else if (mode == 1) {
+          u.gg = ggd;
+          if (!(ggd > 0.0)) {   // g_k = 0: x_k minimises f outright
+            u.stop = GPL1_STOP_STATIONARY;
+            u.iters = k;
+            u.done = 1;
+          }
+        } else if (!(u.kb2p > 0.0)) {   // K g_k = 0 with g_k != 0 cannot happen for g = 2 K^T r
+          u.stop = GPL1_STOP_STATIONARY;
+          u.iters = k;
+          u.done = 1;
+        } else {
+          set_alpha(u.gg / (2.0 * u.kb2p));
+        }
+      }
+      sm.ctl[CTL_INST] = u.done;
+    }
+    csync();
+    if (sm.ctl[CTL_INST]) return false;
+    if (mode == 1) {
+      if constexpr (!kF64) {
+        if (u.xscale != 1.f) {
+          const float xs = u.xscale;
+#pragma unroll
+          for (int j = 0; j < NE; ++j) x[j] *= xs;
+        }
+      } else {
+        if (u.xscale_d != 1.0) {
+          const double xs = u.xscale_d;
+#pragma unroll
+          for (int j = 0; j < NE; ++j) x[j] *= xs;
+        }
+      }
+    }
+    c_gd = S{};
+    c_dd = S{};
+    c_nz = 0;
+    if (mode == 1) {   // the probe pass runs along g_k
+#pragma unroll
+      for (int j = 0; j < NE; ++j) d[j] = g[j];
+      return true;
+    }
+    if (mode == 0) {
+      const A al = kF64 ? static_cast<A>(u.alpha) : static_cast<A>(u.ah);
+      const A th = kF64 ? static_cast<A>(u.tau64) : static_cast<A>(u.th);
+#pragma unroll
+      for (int m = 0; m < NCH; ++m) {
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) {
+          const int j = m * EPC + e;
+          A dn = A(0);
+          if (cv[m]) {
+            const A z = vfma(w, d[j], x[j]);
+            const A v = vfma(-al, gz[j], z);
+            const A mag = vabs(v) - th;
+            const A xn = mag > A(0) ? (v > A(0) ? mag : -mag) : A(0);
+            dn = xn - x[j];
+          }
+          d[j] = dn;
+          if (cid == 0) {
+            acc_mul(c_gd, g[j], dn);
+            acc_mul(c_dd, dn, dn);
+            c_nz |= dn != A(0) ? 1u : 0u;
+          }
+        }
+      }
+      return true;
+    }
+    // mode 2: v = x - alpha g and the threshold of P(v)
+    A v[NE];
+    float th, tl;
+    double t64;
+    int inside;
+    if constexpr (!kF64) {
+      const float ah = u.ah;
+#pragma unroll
+      for (int j = 0; j < NE; ++j) v[j] = fmaf(-ah, g[j], x[j]);
+    } else {
+      const double al = u.alpha;
+#pragma unroll
+      for (int j = 0; j < NE; ++j) v[j] = fma(-al, g[j], x[j]);
+    }
+    tau_search(v, u.hint, u.vbound, th, tl, t64, inside);
+    if constexpr (!kF64) {
+      if (u.acc && !inside) refine_tau(v, th, tl);
+    }
+    csync();
+    if (tid == 0) {
+      u.th = th;
+      u.tl = tl;
+      u.tau64 = t64;
+      u.inside = inside;
+      if (!inside) u.hint = th;
+    }
+    csync();
+    const Dir dr = dir_of();
+#pragma unroll
+    for (int m = 0; m < NCH; ++m) {
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) {
+        const int j = m * EPC + e;
+        d[j] = cv[m] ? dr.d(x[j], g[j]) : A(0);
+        if (cid == 0) {
+          acc_mul(c_gd, g[j], d[j]);
+          acc_mul(c_dd, d[j], d[j]);
+          c_nz |= d[j] != A(0) ? 1u : 0u;
+        }
+      }
+    }
+    return true;
+  }
+
+  // After the pass of a comparison method's step (mode 0 or 2): the step is
+  // taken whole, f_{k+1} = f_k + g_k^T d_k + ||K d_k||^2 (exact for the
+  // quadratic f).  After a PSD probe (mode 1): ||K g_k||^2.  Returns 0
+  // (continue), 1 (stop after the update x + d) or 2 (stop at x_k).
+  __device__ int phase_lm(int k, int s, int mode) {
+    double o[5];
+    unsigned nz = 0;
+    read_parts(s, o, nz);
+    if (tid == 0) {
+      FState& u = sm.st;
+      const SolveParams& P = a.prm;
+      int act = 0;
+      if (!isfinite(o[0]) || !isfinite(o[1]) || !isfinite(o[3])) {
+        u.status = GPL1_ERR_NONFINITE;
+        u.stop = GPL1_STOP_ERROR;
+        u.iters = k;
+        u.done = 1;
+        act = 2;
+      } else if (mode == 1) {
+        u.kb2p = o[1];
+        u.cpass = 0;
+      } else {
+        const double fk = o[0], kb2 = o[1];
+        u.kb2 = kb2;
+        u.gd = o[3];
+        u.dd = o[4];
+        u.cpass = 1;
+        if (!nz) {   // x_{k+1} = x_k: a fixed point of the iteration
+          u.stop = GPL1_STOP_STATIONARY;
+          u.iters = k;
+          u.f_cur = fk;
+          u.done = 1;
+          act = 2;
+        } else {
+          const double fnext = fk + u.gd + kb2;
+          if (P.method != GPL1_METHOD_PSD) u.tau_ss = u.F_cur;   // trace column 3: the objective of eq. 1
+          trace_row(k, fk, 1.0, kb2);
+          if (fabs(fk - fnext) <= kAccDecrease * fk) u.acc = 1;
+          u.lam = 1.0;
+          u.lf = 1.f;
+          u.f_cur = fnext;
+          u.iters = k + 1;
+          if (u.iters >= P.max_iter) {
+            u.stop = GPL1_STOP_MAX_ITER;
+            u.status = GPL1_ERR_NOT_CONVERGED;
+            u.done = 1;
+            act = 1;
+          }
+        }
+      }
+      sm.ctl[CTL_INST] = act;
+    }
+    csync();
+    const int act = sm.ctl[CTL_INST];
+    csync();
+    return act;
+  }
+
+  // The objective of eq. 1 at the returned x after a stop that followed a
+  // whole ISTA / FISTA step (||x||_1 of the new iterate not yet summed).
+  __device__ void eq1_objective_tail() {
+    S l1{};
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+      if constexpr (!kF64) l1 = f2_add(l1, fabsf(x[j]));
+      else l1 += fabs(x[j]);
+    }
+    uint32_t wl[2];
+    put(wl, l1);
+    reduce<Comb<S, 1, 0, 0>>(wl, true);
+    if (tid == 0) {
+      double l1d;
+      if constexpr (!kF64) l1d = as_double(get_f2(wl));
+      else l1d = get_d(wl);
+      sm.st.F_cur = sm.st.f_cur + 2.0 * a.prm.lam_pen * l1d;
+    }
+    csync();
+  }
+
   __device__ void init_state() {
     FState& u = sm.st;
     const SolveParams& P = a.prm;
@@ -1838,6 +2161,8 @@ struct FC {
     u.done = 0;
     u.nz = 0;
     u.tau_steps = 0;
+    u.F_cur = u.gg = u.kb2p = 0.0;
+    u.cpass = 0;
     // with no target to approach, every pass sums K x compensated
     u.acc = (P.stop_rule & (GPL1_STOP_ON_REL_GAP | GPL1_STOP_ON_FW)) ? 0 : 1;
     if (kF64) u.acc = 0;
@@ -1865,30 +2190,50 @@ struct FC {
         x[j] = (cv[m] && !a.x0_zero && gcol[m] + e < p) ? static_cast<A>(xin[gcol[m] + e]) : A(0);
         d[j] = g[j] = u1[j] = u2[j] = A(0);
       }
-    if (!a.x0_zero) project_x0();
+    const bool eq1 = a.prm.method == GPL1_METHOD_ISTA || a.prm.method == GPL1_METHOD_FISTA;
+    if (!a.x0_zero && !eq1) project_x0();   // Alg. GP and PSD start in Omega; eq. 1 has no ball
     int k = 0;
     // setup pass: g_0 = 2 K^T (K x0 - y), f(x0), ||y||^2
     pass<true>(0);
     if (gsync()) {
       phase_l0();
       int s = 0;
+      // One pass per trip.  Alg. GP + SS: projection phase, pass, line search.
+      // ISTA / FISTA: step phase, pass, whole step.  PSD: two trips per
+      // iteration, a probe along g_k (mode 1) and the projected step (mode 2).
+      const bool gpss = a.prm.method == GPL1_METHOD_GPSS;
+      const bool psd = a.prm.method == GPL1_METHOD_PSD;
+      int mode = psd ? 1 : 0;
+      bool tail = false;   // eq. 1: stopped after a whole step (max_iter)
       if (!u.done) {
-        for (k = 0;; ++k) {
+        for (k = 0;;) {
           if (tid == 0 && a.trace) u.ts[0] = globaltimer();
-          if (!phase_p(k, s)) break;   // stop at x_k (FW certificate) or failure
+          // stop at x_k (a stop test or the FW certificate) or failure
+          if (!(gpss ? phase_p(k, s) : phase_m(k, s, mode))) break;
           ++s;
           pass<false>(s);
           if (tid == 0 && a.trace) u.ts[1] = globaltimer();
           if (!gsync()) break;
-          const int act = phase_l(k, s);
-          if (act != 2) {   // x_{k+1} = x_k + lam d_k
+          const int act = gpss ? phase_l(k, s) : phase_lm(k, s, mode);
+          if (mode == 1) {   // PSD probe: x unchanged, the step follows
+            if (act != 0) break;
+            mode = 2;
+            continue;
+          }
+          if (act != 2) {   // x_{k+1} = x_k + lam d_k (lam = 1 for the methods of Sec. 2)
             const A la = kF64 ? static_cast<A>(u.lam) : static_cast<A>(u.lf);
 #pragma unroll
             for (int j = 0; j < NE; ++j) x[j] = vfma(la, d[j], x[j]);
           }
-          if (act != 0) break;
+          if (act != 0) {
+            tail = act == 1;   // the same decision in every CTA (identical scalars)
+            break;
+          }
+          ++k;
+          if (psd) mode = 1;
         }
       }
+      if (eq1 && tail) eq1_objective_tail();
     }
     drain();
     // the solution: cluster 0 writes its copy
@@ -1909,9 +2254,9 @@ struct FC {
       r.stop = (st != GPL1_OK && st != GPL1_ERR_NOT_CONVERGED) ? GPL1_STOP_ERROR : u.stop;
       r.iters = u.iters;
       r.backtracks = u.backtracks;
-      r.f = u.f_cur;
-      r.rel_gap = a.f_star > 0.0 ? (u.f_cur - a.f_star) / a.f_star : -1.0;
-      r.fw_gap = u.gx + a.rho * u.gmax;
+      r.f = eq1 ? u.F_cur : u.f_cur;
+      r.rel_gap = a.f_star > 0.0 ? (r.f - a.f_star) / a.f_star : -1.0;
+      r.fw_gap = eq1 ? -1.0 : u.gx + a.rho * u.gmax;
       r.lambda = 0.5 * u.gmax;
       r.alpha = u.alpha;
       r.tau = kF64 ? u.tau64 : static_cast<double>(u.th) + static_cast<double>(u.tl);

@@ -75,6 +75,8 @@ struct SolveParams {
   double beta, theta, alpha_min, alpha_max, tau1, tol;
   int M, M_alpha, stop_rule, max_iter, max_backtracks, alpha0_rule, debug;
   long long timeout_ns;
+  int method, method_pad;   // GPL1_METHOD_* (the one-read kernel; the others run GPSS only)
+  double lam_pen, step;     // ISTA / FISTA: lambda of eq. 1 and the step s
 };
 
 struct KArgs {

@@ -99,4 +99,16 @@ int lista_pass(PFN_cuTensorMapEncodeTiled_v12000 enc, uint8_t* ws, int* gerr, co
                float* dtheta, double* loss_out, cudaStream_t s);
 cudaError_t lista_adam_step(float* w, const float* g, float* m, float* v, long long count, float lr, int t,
                             cudaStream_t s);
+// W_l = scale K^T for l < L (W: L x p x n FP32; K BF16 n x ldk).
+cudaError_t lista_init_weights(const void* K, long long ldk, int n, int p, int L, float scale, float* W,
+                               cudaStream_t s);
+}  // namespace gpl1
+
+namespace gpl1 {
+// ||K||_2^2 by power iteration (power.cu): `iters` products with K^T K from a
+// fixed start vector; *out (host) receives the Rayleigh quotient of the last
+// unit vector.  ws: power_ws_bytes(n, p, iters) bytes of device memory.
+size_t power_ws_bytes(long long n, long long p, int iters);
+cudaError_t launch_power(int dtype, const void* K, long long ldk, int n, int p, int iters, void* ws, double* out,
+                         cudaStream_t s);
 }  // namespace gpl1

@@ -297,6 +297,34 @@ int lista_pass(PFN_cuTensorMapEncodeTiled_v12000 enc, uint8_t* ws, int* gerr, co
   return static_cast<int>(cudaGetLastError());
 }
 
+// W (p x n, FP32) = scale * K^T for BF16 K (n rows, stride ldk): 32 x 32 tiles
+// through shared memory, coalesced on both sides.
+__global__ void lista_init_w(const uint16_t* __restrict__ K, long long ldk, int n, int p, float scale,
+                             float* __restrict__ W) {
+  __shared__ float t[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;   // rows of K, columns of K
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = r0 + r, j = c0 + threadIdx.x;
+    t[r][threadIdx.x] = (i < n && j < p) ? __uint_as_float(static_cast<uint32_t>(K[i * ldk + j]) << 16) : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = c0 + r, i = r0 + threadIdx.x;
+    if (j < p && i < n) W[static_cast<long long>(j) * n + i] = scale * t[threadIdx.x][r];
+  }
+}
+
+cudaError_t lista_init_weights(const void* K, long long ldk, int n, int p, int L, float scale, float* W,
+                               cudaStream_t s) {
+  const dim3 grid((p + 31) / 32, (n + 31) / 32), block(32, 8);
+  lista_init_w<<<grid, block, 0, s>>>(static_cast<const uint16_t*>(K), ldk, n, p, scale, W);
+  cudaError_t e = cudaGetLastError();
+  const size_t layer = static_cast<size_t>(p) * n * sizeof(float);
+  for (int l = 1; l < L && e == cudaSuccess; ++l)
+    e = cudaMemcpyAsync(reinterpret_cast<uint8_t*>(W) + l * layer, W, layer, cudaMemcpyDeviceToDevice, s);
+  return e;
+}
+
 cudaError_t lista_adam_step(float* w, const float* g, float* m, float* v, long long count, float lr, int t,
                             cudaStream_t s) {
   const float b1 = 0.9f, b2 = 0.999f;

@@ -11,6 +11,7 @@ no decrease of f for 30 iterations).  Nothing here touches the CUDA path.
     python tests/golden/make_golden.py c5       # the radius sweep: c5_fstar.json
     python tests/golden/make_golden.py xstar    # the oracle's solutions x*: xstar_*.npz
     python tests/golden/make_golden.py homotopy # exact minimisers from the homotopy path
+    python tests/golden/make_golden.py c4full   # f* of the 10^4 warm-start test samples
 
 The x* files hold each solution sparsely (indices and values of its nonzero
 entries, FP64), for configs 0-2 and for a seeded sample of the instances of
@@ -207,6 +208,37 @@ def main_xstar(which=("c0", "c1", "c2", "c3a", "c3b", "c4", "c5")):
         print(name, f"{time.time() - t:.0f}s", flush=True)
 
 
+_C4 = {}
+
+
+def _c4full_init():
+    oracle.set_threads(1)
+    _C4["K"], _C4["ldk"] = W.warm_start_K()
+    _C4["Y"], _C4["rho"] = W.warm_start_test()
+
+
+def _c4full_one(q):
+    Ks, ldk = _C4["K"], _C4["ldk"]
+    prob = W.Problem(Ks, Ks.shape[0], 4096, ldk, W.DT_BF16, _C4["Y"][q].copy(), float(_C4["rho"][q]), None, "c4f")
+    return oracle.floor_solve(prob)[1].f
+
+
+def main_c4full(procs=8):
+    """tests/golden/c4full_fstar.json: f* of the 10^4 test samples of the full
+    learned-warm-start configuration (workloads.warm_start_test), by the oracle's
+    floor solve, one single-threaded solve per worker process."""
+    import multiprocessing as mp
+    out = os.path.join(os.path.dirname(OUT), "c4full_fstar.json")
+    t = time.time()
+    count = W.WARM_TEST_FULL
+    with mp.get_context("spawn").Pool(procs, initializer=_c4full_init) as pool:
+        fs = pool.map(_c4full_one, range(count), chunksize=16)
+    print(len(fs), f"{time.time() - t:.0f}s", flush=True)
+    with open(out, "w") as fh:
+        json.dump({"workload": f"c4_warmstart1024x4096_bf16_test{count}", "f_star": fs,
+                   "solver": "oracle.floor_solve"}, fh, indent=0)
+
+
 HOMOTOPY_CASES = [(0, 30, 60, 6), (1, 30, 60, 6), (2, 40, 120, 8), (3, 50, 40, 5), (4, 20, 200, 4),
                   (5, 64, 64, 10)]
 
@@ -233,6 +265,9 @@ def main_homotopy():
 
 if __name__ == "__main__":
     args = sys.argv[1:]
+    if args == ["c4full"]:
+        main_c4full()
+        sys.exit(0)
     if args == ["homotopy"]:
         main_homotopy()
         sys.exit(0)

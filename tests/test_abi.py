@@ -46,7 +46,8 @@ def test_struct_layouts_match_header(tmp_path):
 #include "{HEADER}"
 int main(void) {{
   printf("%zu %zu %zu\\n", sizeof(gpl1_params), sizeof(gpl1_result), sizeof(gpl1_problem));
-  printf("%zu %zu %zu\\n", offsetof(gpl1_params, timeout_ns), offsetof(gpl1_result, fail_iter), offsetof(gpl1_problem, trace_cap));
+  printf("%zu %zu %zu %zu %zu\\n", offsetof(gpl1_params, timeout_ns), offsetof(gpl1_result, fail_iter), offsetof(gpl1_problem, trace_cap),
+         offsetof(gpl1_params, method), offsetof(gpl1_params, step));
   return 0;
 }}''')
     exe = tmp_path / "sz"
@@ -55,7 +56,8 @@ int main(void) {{
     assert [int(v) for v in a.split()] == [ctypes.sizeof(pkg.Params), ctypes.sizeof(pkg.Result),
                                            ctypes.sizeof(pkg.Problem)]
     assert [int(v) for v in b.split()] == [pkg.Params.timeout_ns.offset, pkg.Result.fail_iter.offset,
-                                           pkg.Problem.trace_cap.offset]
+                                           pkg.Problem.trace_cap.offset, pkg.Params.method.offset,
+                                           pkg.Params.step.offset]
 
 
 def test_null_context_is_rejected_without_a_gpu():

@@ -111,3 +111,17 @@ def test_homotopy_walk_at_several_radii_equals_single_walks():
     for r, (x, lam, seg) in zip(radii, many):
         x1, lam1, seg1 = homotopy.solve_at_radius(K, y, r)
         assert np.array_equal(x, x1) and lam == lam1 and seg == seg1
+
+
+def test_stored_optima_of_the_full_warm_start_test_set():
+    """tests/golden/c4full_fstar.json (10^4 warm-start test samples): three entries
+    recomputed by the oracle's floor solve, and every value positive and finite."""
+    gold = json.load(open(os.path.join(GOLD, "c4full_fstar.json")))
+    fs = gold["f_star"]
+    assert len(fs) == W.WARM_TEST_FULL and all(np.isfinite(fs)) and min(fs) > 0
+    Ks, ldk = W.warm_start_K()
+    Y, rho = W.warm_start_test()
+    for q in (0, 5000, W.WARM_TEST_FULL - 1):
+        prob = W.Problem(Ks, Ks.shape[0], 4096, ldk, W.DT_BF16, Y[q].copy(), float(rho[q]), None, f"c4f_{q}")
+        f = oracle.floor_solve(prob)[1].f
+        assert abs(f - fs[q]) <= 1e-12 * fs[q], (q, f, fs[q])

@@ -256,3 +256,26 @@ def test_nonmonotone_line_search_matches_oracle(gpu_ctx):
     x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000, M=10)
     assert res.status == 0, res.as_dict()
     assert rel_gap(prob, x, rs.f) <= 1e-6
+
+
+def test_engine_autotuner_picks_lists_and_agrees(gpu_ctx):
+    """GPL1_ENGINE_AUTO times the admissible engines once per shape and keeps the
+    fastest (gpl1_solve_tuned lists it); every engine, pinned, reaches the same
+    optimum."""
+    prob = small(1024, 8192, 40, W.DT_F32, seed=77)
+    xs, rs, _ = oracle.reference_solve(prob)
+    before = len(gpu_ctx.solve_tuned())
+    x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000,
+                       engine=pkg.ENGINE_AUTO)
+    tuned = gpu_ctx.solve_tuned()
+    assert len(tuned) == before + 1
+    entry = [t for t in tuned if t["shape"] == (W.DT_F32, 1024, 8192, 0)][0]
+    assert entry["engine"] in (pkg.ENGINE_TWO_PASS, pkg.ENGINE_ONE_READ_NCH1, pkg.ENGINE_ONE_READ_NCH2)
+    assert entry["ms"] > 0
+    assert res.status == 0 and rel_gap(prob, x, rs.f) <= 1e-6
+    for eng in (pkg.ENGINE_TWO_PASS, pkg.ENGINE_ONE_READ_NCH1, pkg.ENGINE_ONE_READ_NCH2):
+        x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000,
+                           engine=eng)
+        assert res.status == 0 and rel_gap(prob, x, rs.f) <= 1e-6, eng
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-3
+    assert len(gpu_ctx.solve_tuned()) == before + 1   # pinned engines do not tune

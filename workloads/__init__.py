@@ -238,6 +238,25 @@ def warm_start_train(count: int = 65536, n: int = 1024, p: int = 4096, k: int = 
     return Y, rho
 
 
+# The full learned-warm-start configuration: 10^5 training and 10^4 test
+# right-hand sides on the K of warm_start_data, from separate streams.
+WARM_TRAIN_FULL, WARM_TEST_FULL = 100_000, 10_000
+
+
+def warm_start_test(count: int = WARM_TEST_FULL, n: int = 1024, p: int = 4096, k: int = 50, *,
+                    seed: int = SEED_BASE + 8, sigma: float = 0.01):
+    """Test right-hand sides of the full learned-warm-start configuration, drawn as
+    warm_start_train draws its samples but from their own stream.  Returns
+    (Y float32 count x n, rho float64 count)."""
+    return warm_start_train(count, n, p, k, seed=seed, sigma=sigma)
+
+
+def warm_start_K(n: int = 1024, p: int = 4096):
+    """(K stored n x ldk BF16 bits, ldk): the K of the learned-warm-start workload."""
+    Ks, ldk, _, _, _ = warm_start_data(n, p, 1, 50)
+    return Ks, ldk
+
+
 def lista_exact_case(seed: int = 3, n: int = 64, p: int = 128, B: int = 64, L: int = 2):
     """Learned-warm-start data on which BF16 operands and FP32 sums lose nothing:
     K with one +-1 per column, W_l with one entry in {+-1, +-1/2} per row, y
