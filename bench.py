@@ -708,7 +708,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "frac_of_nominal_8tbs": achieved / 8000.0,
-                     "kernel": "gpl1::fz::fused_kernel<1,1> (one-read engine)",
+                     "kernel": "gpl1::fz::fused_kernel<1,2> (one-read engine, two column chunks per thread)",
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "algorithmic_bytes": "one read of K (n p 4 B) per pass; passes = iterations + 1",
                      "kernel_ms": kms},

@@ -58,7 +58,12 @@ typedef enum {
   GPL1_STOP_STATIONARY = 1, /* P(x - alpha g) == x exactly: stationary (Alg. GP, Step 2) */
   GPL1_STOP_FW = 2,         /* Frank-Wolfe certificate (g^T x + rho ||g||_inf) <= tol (f - cert) */
   GPL1_STOP_MAX_ITER = 3,
-  GPL1_STOP_ERROR = 4       /* see gpl1_result.status                                */
+  GPL1_STOP_ERROR = 4,      /* see gpl1_result.status                                */
+  GPL1_STOP_STAGNATION = 5  /* float data (one-read single solve, shared-K form): f
+                               stopped falling near the stop (by 1e-3 tol of the gap
+                               denominator) for 64 (single solve) or 32 (shared-K)
+                               iterations before the rule held: the precision floor of
+                               the FP32 path; status GPL1_ERR_NOT_CONVERGED           */
 } gpl1_stop;
 
 /* Stop rules (gpl1_params.stop_rule, a bit set; the solve stops at the first that holds). */
@@ -127,11 +132,11 @@ typedef struct {
  *    forms K x_k and K d_k also forms 2 K^T (K x_k - y) and 2 K^T K d_k from
  *    the same tiles, and g_{k+1} is their combination with the Armijo step
  *    (Alg. GP, Steps 5-6).  A cluster of C CTAs covers the p columns, each CTA
- *    a slice of W columns (one 16-byte chunk per thread: W = 2048 F32, 4096
- *    BF16, 1024 F64; or two chunks, twice that and half the cluster), up to
- *    C = 16.  ONE_READ lets the autotuner pick the chunks per thread;
- *    ONE_READ_NCH1 and ONE_READ_NCH2 fix them.  GPL1_ERR_UNSUPPORTED when the
- *    instance does not fit.
+ *    a slice of W columns held by its 256 consumer threads, each with two
+ *    16-byte chunks of columns (W = 2048 F32, 4096 BF16, 1024 F64) or four
+ *    (twice that, half the cluster), up to C = 16.  ONE_READ lets the
+ *    autotuner pick the chunks per thread; ONE_READ_NCH2 and ONE_READ_NCH4 fix
+ *    them.  GPL1_ERR_UNSUPPORTED when the instance does not fit.
  *  TWO_PASS: one persistent cooperative launch that reads K twice per
  *    iteration (K^T r, then [K d, K x]); p up to 16800 F32/BF16, 3840 F64.
  *  AUTO: the autotuner picks among all engines that fit.
@@ -143,8 +148,8 @@ typedef struct {
 #define GPL1_ENGINE_AUTO 0
 #define GPL1_ENGINE_ONE_READ 1
 #define GPL1_ENGINE_TWO_PASS 2
-#define GPL1_ENGINE_ONE_READ_NCH1 3
-#define GPL1_ENGINE_ONE_READ_NCH2 4
+#define GPL1_ENGINE_ONE_READ_NCH2 3
+#define GPL1_ENGINE_ONE_READ_NCH4 4
 
 typedef struct {
   int status;          /* gpl1_status of this instance                                 */
@@ -307,8 +312,8 @@ int gpl1_gemm_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* confi
 /* The single-solve autotuner's choices (gpl1_params.engine AUTO / ONE_READ):
  * returns the number of tuned shapes (-1 for a NULL ctx); for 0 <= index <
  * that number it also writes shape[4] = {dtype, n, p, 0 for AUTO or 1 for
- * ONE_READ}, the engine chosen (GPL1_ENGINE_TWO_PASS, _ONE_READ_NCH1 or
- * _ONE_READ_NCH2) and its time for the tuning solve (ms).  Any output pointer
+ * ONE_READ}, the engine chosen (GPL1_ENGINE_TWO_PASS, _ONE_READ_NCH2 or
+ * _ONE_READ_NCH4) and its time for the tuning solve (ms).  Any output pointer
  * may be NULL. */
 int gpl1_solve_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* engine, float* ms);
 

@@ -21,10 +21,10 @@ LIB_PATH = os.path.join(HERE, "lib", "libgpl1.so")
 F64, F32, BF16 = 0, 1, 2
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NOT_CONVERGED", 4: "LINESEARCH", 5: "NONFINITE",
           6: "TIMEOUT", 7: "UNSUPPORTED"}
-STOP = {0: "rel_gap", 1: "stationary", 2: "fw", 3: "max_iter", 4: "error"}
+STOP = {0: "rel_gap", 1: "stationary", 2: "fw", 3: "max_iter", 4: "error", 5: "stagnation"}
 STOP_ON_REL_GAP, STOP_ON_FW = 1, 2
 DEBUG_UNREACHABLE_BARRIER = 1
-ENGINE_AUTO, ENGINE_ONE_READ, ENGINE_TWO_PASS, ENGINE_ONE_READ_NCH1, ENGINE_ONE_READ_NCH2 = 0, 1, 2, 3, 4
+ENGINE_AUTO, ENGINE_ONE_READ, ENGINE_TWO_PASS, ENGINE_ONE_READ_NCH2, ENGINE_ONE_READ_NCH4 = 0, 1, 2, 3, 4
 METHOD_GPSS, METHOD_ISTA, METHOD_FISTA, METHOD_PSD = 0, 1, 2, 3
 TRACE_COLS = 28
 # statuses that describe how a solve ended (reported in Result.status, not raised)

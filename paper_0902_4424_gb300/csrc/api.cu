@@ -135,7 +135,7 @@ gpl1_status check_params(gpl1_ctx* ctx, const gpl1_params* p, bool methods = fal
   if (p->max_iter < 1 || p->max_backtracks < 0) return fail(ctx, GPL1_ERR_INVALID_ARG, "bad max_iter/max_backtracks");
   if (p->timeout_ns <= 0) return fail(ctx, GPL1_ERR_INVALID_ARG, "timeout_ns must be > 0");
   if (p->alpha0_rule != 0 && p->alpha0_rule != 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "alpha0_rule is 0 or 1");
-  if (p->engine < GPL1_ENGINE_AUTO || p->engine > GPL1_ENGINE_ONE_READ_NCH2)
+  if (p->engine < GPL1_ENGINE_AUTO || p->engine > GPL1_ENGINE_ONE_READ_NCH4)
     return fail(ctx, GPL1_ERR_INVALID_ARG, "engine must be one of GPL1_ENGINE_*");
   return GPL1_OK;
 }
@@ -535,7 +535,7 @@ gpl1_status one_read_choose(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, OneRe
     nch = want_nch;
     C = static_cast<int>(c);
   }
-  for (int cand : {1, 2}) {
+  for (int cand : {2, 4}) {
     if (nch) break;
     const long long w = fused_width(dt, cand);
     const long long c = (p + w - 1) / w;
@@ -546,12 +546,12 @@ gpl1_status one_read_choose(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, OneRe
     }
   }
   if (!nch) {
-    const long long w = fused_width(dt, 2);
+    const long long w = fused_width(dt, 4);
     const long long c = (p + w - 1) / w;
     if (c > fz::kCMax)
       return fail(ctx, GPL1_ERR_UNSUPPORTED, "p = %lld exceeds the one-read kernel's %lld columns", p,
                   static_cast<long long>(fz::kCMax) * w);
-    nch = 2;
+    nch = 4;
     C = static_cast<int>(c);
   }
   const std::vector<int> key = {dt, nch, C};
@@ -663,7 +663,7 @@ gpl1_status tune_engine(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl
         st = run(ctx, &tp, 1, dt, &tq, &r);
       } else {
         OneRead o;
-        if ((st = one_read_choose(ctx, &tp, dt, &o, eng == GPL1_ENGINE_ONE_READ_NCH2 ? 2 : 1))) return st;
+        if ((st = one_read_choose(ctx, &tp, dt, &o, eng == GPL1_ENGINE_ONE_READ_NCH4 ? 4 : 2))) return st;
         st = run_one_read(ctx, &tp, dt, &tq, o, &r, nullptr);
       }
       if (st != GPL1_OK && st != GPL1_ERR_NOT_CONVERGED && st != GPL1_ERR_LINESEARCH) return st;
@@ -690,18 +690,18 @@ gpl1_status pick_engine(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl
   if (st) return st;
   if (pr->n > (1LL << 30) || pr->p > (1LL << 30)) return fail(ctx, GPL1_ERR_UNSUPPORTED, "n or p too large");
   GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-  if (prm->engine == GPL1_ENGINE_ONE_READ_NCH1 || prm->engine == GPL1_ENGINE_ONE_READ_NCH2) {
-    if ((st = one_read_choose(ctx, pr, dt, o, prm->engine == GPL1_ENGINE_ONE_READ_NCH2 ? 2 : 1))) return st;
+  if (prm->engine == GPL1_ENGINE_ONE_READ_NCH2 || prm->engine == GPL1_ENGINE_ONE_READ_NCH4) {
+    if ((st = one_read_choose(ctx, pr, dt, o, prm->engine == GPL1_ENGINE_ONE_READ_NCH4 ? 4 : 2))) return st;
     *use_one_read = true;
     return GPL1_OK;
   }
   // the admissible candidates
   std::vector<int> cands;
   gpl1_status last = GPL1_OK;
-  for (int nch : {1, 2}) {
+  for (int nch : {2, 4}) {
     OneRead t;
     const gpl1_status s1 = one_read_choose(ctx, pr, dt, &t, nch);
-    if (s1 == GPL1_OK) cands.push_back(nch == 1 ? GPL1_ENGINE_ONE_READ_NCH1 : GPL1_ENGINE_ONE_READ_NCH2);
+    if (s1 == GPL1_OK) cands.push_back(nch == 2 ? GPL1_ENGINE_ONE_READ_NCH2 : GPL1_ENGINE_ONE_READ_NCH4);
     else last = s1;
   }
   const bool two_ok = prm->engine == GPL1_ENGINE_AUTO && prm->method == GPL1_METHOD_GPSS &&
@@ -719,7 +719,7 @@ gpl1_status pick_engine(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl
     }
   }
   if (eng == GPL1_ENGINE_TWO_PASS) return check_problem(ctx, pr, dt, 0, true);
-  if ((st = one_read_choose(ctx, pr, dt, o, eng == GPL1_ENGINE_ONE_READ_NCH2 ? 2 : 1))) return st;
+  if ((st = one_read_choose(ctx, pr, dt, o, eng == GPL1_ENGINE_ONE_READ_NCH4 ? 4 : 2))) return st;
   *use_one_read = true;
   return GPL1_OK;
 }
@@ -1259,6 +1259,16 @@ extern "C" gpl1_status gpl1_solve_shared_k(gpl1_ctx* ctx, const void* K, long lo
   GPL1_CUDA(cudaMemsetAsync(G[1], 0, N * pp * 4, s), "cudaMemsetAsync");
   GPL1_CUDA(cudaMemcpyAsync(rho_d, rho, N * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(rho)");
   if (f_star) GPL1_CUDA(cudaMemcpyAsync(fs_d, f_star, N * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(f*)");
+  {   // every result slot starts as "not converged"; phase L overwrites it when its instance stops
+    std::vector<gpl1_result> init(N);
+    for (gpl1_result& r : init) {
+      std::memset(&r, 0, sizeof r);
+      r.status = GPL1_ERR_NOT_CONVERGED;
+      r.stop = GPL1_STOP_MAX_ITER;
+    }
+    GPL1_CUDA(cudaMemcpyAsync(rdev, init.data(), N * sizeof(gpl1_result), cudaMemcpyHostToDevice, s),
+              "cudaMemcpyAsync(results)");   // pageable source: staged before the call returns
+  }
   const SolveParams sp = to_kernel_params(prm);
   if (!ctx->ev[0]) {
     GPL1_CUDA(cudaEventCreate(&ctx->ev[0]), "cudaEventCreate");

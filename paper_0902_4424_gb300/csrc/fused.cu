@@ -12,25 +12,25 @@ const void* kernel_ptr() {
 }
 
 const void* fused_ptr(int dt, int nch) {
-  switch (dt * 4 + nch) {
-    case GPL1_F64 * 4 + 1: return kernel_ptr<GPL1_F64, 1>();
-    case GPL1_F64 * 4 + 2: return kernel_ptr<GPL1_F64, 2>();
-    case GPL1_F32 * 4 + 1: return kernel_ptr<GPL1_F32, 1>();
-    case GPL1_F32 * 4 + 2: return kernel_ptr<GPL1_F32, 2>();
-    case GPL1_BF16 * 4 + 1: return kernel_ptr<GPL1_BF16, 1>();
-    case GPL1_BF16 * 4 + 2: return kernel_ptr<GPL1_BF16, 2>();
+  switch (dt * 8 + nch) {
+    case GPL1_F64 * 8 + 2: return kernel_ptr<GPL1_F64, 2>();
+    case GPL1_F64 * 8 + 4: return kernel_ptr<GPL1_F64, 4>();
+    case GPL1_F32 * 8 + 2: return kernel_ptr<GPL1_F32, 2>();
+    case GPL1_F32 * 8 + 4: return kernel_ptr<GPL1_F32, 4>();
+    case GPL1_BF16 * 8 + 2: return kernel_ptr<GPL1_BF16, 2>();
+    case GPL1_BF16 * 8 + 4: return kernel_ptr<GPL1_BF16, 4>();
     default: return nullptr;
   }
 }
 
 size_t smem_of(int dt, int nch) {
-  switch (dt * 4 + nch) {
-    case GPL1_F64 * 4 + 1: return fz::fused_smem_bytes<GPL1_F64, 1>();
-    case GPL1_F64 * 4 + 2: return fz::fused_smem_bytes<GPL1_F64, 2>();
-    case GPL1_F32 * 4 + 1: return fz::fused_smem_bytes<GPL1_F32, 1>();
-    case GPL1_F32 * 4 + 2: return fz::fused_smem_bytes<GPL1_F32, 2>();
-    case GPL1_BF16 * 4 + 1: return fz::fused_smem_bytes<GPL1_BF16, 1>();
-    case GPL1_BF16 * 4 + 2: return fz::fused_smem_bytes<GPL1_BF16, 2>();
+  switch (dt * 8 + nch) {
+    case GPL1_F64 * 8 + 2: return fz::fused_smem_bytes<GPL1_F64, 2>();
+    case GPL1_F64 * 8 + 4: return fz::fused_smem_bytes<GPL1_F64, 4>();
+    case GPL1_F32 * 8 + 2: return fz::fused_smem_bytes<GPL1_F32, 2>();
+    case GPL1_F32 * 8 + 4: return fz::fused_smem_bytes<GPL1_F32, 4>();
+    case GPL1_BF16 * 8 + 2: return fz::fused_smem_bytes<GPL1_BF16, 2>();
+    case GPL1_BF16 * 8 + 4: return fz::fused_smem_bytes<GPL1_BF16, 4>();
     default: return 0;
   }
 }

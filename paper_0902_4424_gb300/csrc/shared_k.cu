@@ -55,7 +55,17 @@ struct MrState {
   int inside, nz, iters, backtracks, stop, status, done, acc, acc_age;
   double f_cur, gap_den, f_star, rho, lam, gd, dd, gx;
   double fhist[kMaxM];
+  double f_best;   // lowest f so far, and the iterations since it last fell by a
+  int stall;       // meaningful amount (the stagnation stop near the precision floor)
 };
+
+// Stagnation (with a stop rule to reach): near the stop (acc), an instance
+// whose f has not fallen by more
+// than 1e-3 tol of its gap denominator for this many iterations sits at the
+// precision floor of the FP32 form (its carried and exact residuals disagree
+// by about the tolerance) and stops, not converged, instead of running to
+// max_iter and holding the whole batch.
+constexpr int kMrStallIters = 32;
 
 // The staged vector comes last: a launch allocates only its first
 // ceil(p / 480) * 480 entries, so that for p = 8192 four CTAs share an SM.
@@ -143,6 +153,7 @@ __global__ void __launch_bounds__(kConsumers) mr_init(const float* Y, long long 
     s.ss.tau_ss = static_cast<float>(prm.tau1);
     const double y2 = as_double(v[0]);
     s.f_cur = y2;
+    s.f_best = y2;
     for (int q = 0; q < kMaxM; ++q) s.fhist[q] = y2;
     s.rho = rho[b];
     const F2 rp = f2_of(rho[b]);
@@ -227,6 +238,7 @@ __global__ void __launch_bounds__(kConsumers) mr_setup_r(const float* KDX, const
     s.ss.tau_ss = static_cast<float>(prm.tau1);
     const double f0 = as_double(v[0]), y2 = as_double(v[1]);
     s.f_cur = f0;
+    s.f_best = f0;
     for (int q = 0; q < kMaxM; ++q) s.fhist[q] = f0;
     s.rho = rho[b];
     const F2 rp = f2_of(rho[b]);
@@ -723,17 +735,32 @@ __global__ void __launch_bounds__(kConsumers) mr_phase_l(float* KD, int splits, 
         if ((S.f_star >= 0.0 && fnext - S.f_star <= 1e3 * prm.tol * S.gap_den) || fk - fnext <= 1e-4 * fk) S.acc = 1;
         const bool gap_met =
             (prm.stop_rule & GPL1_STOP_ON_REL_GAP) && S.f_star >= 0.0 && fnext - S.f_star <= prm.tol * S.gap_den;
+        if (fnext < S.f_best - 1e-3 * prm.tol * S.gap_den) {
+          S.f_best = fnext;
+          S.stall = 0;
+        } else {
+          ++S.stall;
+        }
         // f from the exact K x of this iterate
         if (gap_met && exact) {
           S.stop = GPL1_STOP_REL_GAP;
           S.done = 1;
-        } else if (gap_met) {   // f from the carried r: confirm on an exact K x next iteration
-          S.acc = 1;
-          S.acc_age = 0;
-        } else if (S.iters >= prm.max_iter) {
-          S.stop = GPL1_STOP_MAX_ITER;
-          S.status = GPL1_ERR_NOT_CONVERGED;
-          S.done = 1;
+        } else {
+          if (gap_met) {   // f from the carried r: confirm on an exact K x next iteration
+            S.acc = 1;
+            S.acc_age = 0;
+          }
+          // the last iteration ends every instance still running, whatever its state
+          if (S.iters >= prm.max_iter) {
+            S.stop = GPL1_STOP_MAX_ITER;
+            S.status = GPL1_ERR_NOT_CONVERGED;
+            S.done = 1;
+          } else if (S.acc && S.stall >= kMrStallIters &&
+                     (prm.stop_rule & (GPL1_STOP_ON_REL_GAP | GPL1_STOP_ON_FW))) {
+            S.stop = GPL1_STOP_STAGNATION;
+            S.status = GPL1_ERR_NOT_CONVERGED;
+            S.done = 1;
+          }
         }
       }
     }

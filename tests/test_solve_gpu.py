@@ -219,15 +219,15 @@ def test_largest_p_the_kernel_stages(gpu_ctx, dtype, p):
 
 
 # columns the one-read engine takes at most: 16 CTAs per cluster, each with
-# two 16-byte chunks per thread of its 512 consumer threads
-ONE_READ_MAX_P = {W.DT_F32: 16 * 2 * 512 * 4, W.DT_F64: 16 * 2 * 512 * 2, W.DT_BF16: 16 * 2 * 512 * 8}
+# four 16-byte chunks per thread of its 256 consumer threads
+ONE_READ_MAX_P = {W.DT_F32: 16 * 4 * 256 * 4, W.DT_F64: 16 * 4 * 256 * 2, W.DT_BF16: 16 * 4 * 256 * 8}
 
 
 @pytest.mark.parametrize("dtype,p", [(W.DT_F32, 24000), (W.DT_F64, 9000)])
 def test_one_read_engine_beyond_the_two_pass_limit(gpu_ctx, dtype, p):
-    """Past the two-pass limit (two chunks per thread, clusters of 6 and 5
-    CTAs): the one-read engine reaches the oracle's optimum; past its own
-    limit it refuses with GPL1_ERR_UNSUPPORTED."""
+    """Past the two-pass limit (clusters of 12 or 6 CTAs for F32, 9 or 5 for
+    F64, as the autotuner picks): the one-read engine reaches the oracle's
+    optimum; past its own limit it refuses with GPL1_ERR_UNSUPPORTED."""
     prob = small(192, p, 16, dtype, seed=p + 7 * dtype, rho_scale=0.8)
     xs, rs, _ = oracle.reference_solve(prob)
     x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000,
@@ -270,12 +270,36 @@ def test_engine_autotuner_picks_lists_and_agrees(gpu_ctx):
     tuned = gpu_ctx.solve_tuned()
     assert len(tuned) == before + 1
     entry = [t for t in tuned if t["shape"] == (W.DT_F32, 1024, 8192, 0)][0]
-    assert entry["engine"] in (pkg.ENGINE_TWO_PASS, pkg.ENGINE_ONE_READ_NCH1, pkg.ENGINE_ONE_READ_NCH2)
+    assert entry["engine"] in (pkg.ENGINE_TWO_PASS, pkg.ENGINE_ONE_READ_NCH2, pkg.ENGINE_ONE_READ_NCH4)
     assert entry["ms"] > 0
     assert res.status == 0 and rel_gap(prob, x, rs.f) <= 1e-6
-    for eng in (pkg.ENGINE_TWO_PASS, pkg.ENGINE_ONE_READ_NCH1, pkg.ENGINE_ONE_READ_NCH2):
+    for eng in (pkg.ENGINE_TWO_PASS, pkg.ENGINE_ONE_READ_NCH2, pkg.ENGINE_ONE_READ_NCH4):
         x, res = gpu_solve(gpu_ctx, prob, stop_rule=pkg.STOP_ON_REL_GAP, tol=5e-7, f_star=rs.f, max_iter=20000,
                            engine=eng)
         assert res.status == 0 and rel_gap(prob, x, rs.f) <= 1e-6, eng
         assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-3
     assert len(gpu_ctx.solve_tuned()) == before + 1   # pinned engines do not tune
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("name", ["c1", "c2"])
+def test_fp32_trace_follows_the_fp64_oracle(gpu_ctx, name, engine):
+    """FP32 data, full size: over the first 25 iterations the kernels take the
+    oracle's decisions (the same Armijo steps lambda_k and Alg. SS ratio-test
+    branches, so the same tau_k) and their steplengths alpha_k stay within 1e-3
+    of the FP64 oracle's (measured: 2e-4), f_k within 1e-4.  Alg. SS and the
+    line search run in FP64 on float-pair sums, so FP32 rounding enters only
+    through the products with K."""
+    prob = W.config1() if name == "c1" else W.config2()
+    N = 25
+    xo, ro, to = oracle.gpss(prob, trace=True, tol=0.0, max_iter=N)
+    K, y = to_dev(prob)
+    tr = torch.zeros(N, pkg.TRACE_COLS, dtype=torch.float64, device=DEV)
+    prm = pkg.params_default(stop_rule=0, max_iter=N, engine=engine, x0_is_zero=1)
+    _, res = gpu_ctx.solve(K, y, prob.rho, p=prob.p, params=prm, trace=tr)
+    t = tr.cpu().numpy()
+    assert res.iters == N
+    np.testing.assert_array_equal(t[:, 2], to[:, 2])                    # lambda_k
+    np.testing.assert_allclose(t[:, 3], to[:, 3], rtol=1e-6, atol=0)    # tau_k of Alg. SS
+    np.testing.assert_allclose(t[:, 1], to[:, 1], rtol=1e-3, atol=0)    # alpha_k
+    np.testing.assert_allclose(t[:, 0], to[:, 0], rtol=1e-4, atol=0)    # f(x_k)
