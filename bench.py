@@ -586,8 +586,10 @@ def run_ours(args, rank, world, local_rank):
     y = y_host.to(dev)
     x = torch.zeros(p, dtype=torch.float32, device=dev)
     ctx = pkg.Context(local_rank)
+    engine = {"one_read": pkg.ENGINE_ONE_READ, "nch2": pkg.ENGINE_ONE_READ_NCH2, "nch4": pkg.ENGINE_ONE_READ_NCH4,
+              "two_pass": pkg.ENGINE_TWO_PASS, "auto": pkg.ENGINE_AUTO}[args.engine]
     prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=TOL, f_star=fstar, x0_is_zero=1, max_iter=20000,
-                             engine=pkg.ENGINE_ONE_READ)
+                             engine=engine)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MiB > L2
 
     def solve():
@@ -698,6 +700,7 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": prob.name, "n": n, "p": p, "rho": prob.rho, "stop": f"rel_gap<={TOL:g} vs oracle f*",
+                   "engine": args.engine,
                    "x0": "zero", "l2": "K (256 MiB) exceeds L2; 512 MiB flush between steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "iters_per_solve": mean_iters,
@@ -911,6 +914,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--engine", choices=["one_read", "nch2", "nch4", "two_pass", "auto"], default="one_read",
+                    help="the main solve's engine (one_read: the autotuner picks the chunks per thread; a "
+                         "fixed choice for profiling, which distorts the tuner's timings)")
     ap.add_argument("--batched-sample", type=int, default=512,
                     help="also time this many ragged instances batched vs plain (0: skip)")
     ap.add_argument("--shared-k", type=int, default=1024,
