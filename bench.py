@@ -287,6 +287,25 @@ def run_batched(count, steps, dev, plain_sample=64):
            "verified_max_rel_gap": max(gaps) if gaps else None, "verified_instances": len(gaps),
            "hbm_gbs": algo / (statistics.mean(kms) / 1e3) / 1e9}
     out["roofline_frac"] = out["hbm_gbs"] / peak
+    # the box shape the batched autotuner chose for this batch (its 4-iteration
+    # timings) and, for comparison, the whole batched solve with each shape pinned
+    names = {pkg.TILE_SMALL: "small_15KiB", pkg.TILE_MEDIUM: "medium_30KiB", pkg.TILE_LARGE: "large_60KiB"}
+    tuned = [t for t in ctx.batched_tuned() if t["key"][1] == count]
+    if tuned:
+        out["tile_tuned"] = {"choice": names[tuned[0]["tile"]],
+                             "tuning_ms": {names[k]: round(v, 4) for k, v in
+                                           zip((pkg.TILE_SMALL, pkg.TILE_MEDIUM, pkg.TILE_LARGE), tuned[0]["ms"])}}
+    pinned = {}
+    for tl, nm in names.items():
+        q = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=0.5 * TOL, x0_is_zero=1, max_iter=20000, tile=tl)
+        ctx.solve_batched(descs, pkg.BF16, q)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rr = ctx.solve_batched(descs, pkg.BF16, q)
+        b.record(stream)
+        b.synchronize()
+        pinned[nm] = {"ms_per_batch": round(a.elapsed_time(b), 3), "ok": sum(r.status == 0 for r in rr)}
+    out["tile_pinned"] = pinned
     ctx.close()
     return out
 

@@ -104,7 +104,31 @@ typedef struct {
   double step;         /* ISTA, FISTA: step s > 0 of x + s K^T (y - K x) thresholded at
                           s lambda; 1 is the paper's iteration (||K|| < 1), 1/||K||^2
                           (gpl1_spectral_norm_sq) admits any K                         */
+  int tile;            /* box shape of the two-pass kernel (GPL1_TILE_*): AUTO lets the
+                          batched calls tune it per batch (gpl1_batched_tuned) and
+                          gives MEDIUM to single solves; gpl1_solve_noalloc always
+                          runs MEDIUM                                                 */
+  int tile_pad;        /* 0 */
 } gpl1_params;
+
+/* gpl1_params.tile: the two-pass kernel streams K in TMA boxes of RB rows x
+ * 256 columns through a 120 KiB shared-memory ring; RB rows split evenly over
+ * its 15 consumer warps.
+ *   SMALL:  15 KiB boxes, 8 stages (RB = 15 F32, 30 BF16; no F64 shape)
+ *   MEDIUM: 30 KiB boxes, 4 stages (RB = 15 F64, 30 F32, 60 BF16)
+ *   LARGE:  60 KiB boxes, 2 stages (RB = 30 F64, 60 F32, 120 BF16)
+ * Smaller boxes pad ragged row counts less and spread an instance over more
+ * units; larger ones take fewer waits and reductions per byte.  AUTO: the
+ * first time a context meets a batch (dtype and the list of instance shapes),
+ * gpl1_solve_batched, gpl1_solve_batched_async and gpl1_plan_create time
+ * every admissible shape on the batch itself (four iterations into scratch
+ * copies of x, twice; the faster second run wins) and keep the choice for the
+ * context; that first call synchronises the stream.  A shape given here is used
+ * as is (GPL1_ERR_UNSUPPORTED for SMALL with F64 data). */
+#define GPL1_TILE_AUTO 0
+#define GPL1_TILE_SMALL 1
+#define GPL1_TILE_MEDIUM 2
+#define GPL1_TILE_LARGE 3
 
 /* gpl1_params.method: the iterations of Sec. 2 on the one-read kernel's passes
  * (each pass forms K v and 2 K^T (K x - y), 2 K^T K v for the pass's direction v
@@ -316,6 +340,14 @@ int gpl1_gemm_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* confi
  * _ONE_READ_NCH4) and its time for the tuning solve (ms).  Any output pointer
  * may be NULL. */
 int gpl1_solve_tuned(const gpl1_ctx* ctx, int index, long long* shape, int* engine, float* ms);
+
+/* The batched autotuner's choices (gpl1_params.tile AUTO): returns the number
+ * of tuned batches (-1 for a NULL ctx); for 0 <= index < that number it also
+ * writes key[4] = {dtype, instances, sum of n p over the instances, largest
+ * n p}, the tile chosen (GPL1_TILE_*) and the time of each candidate's tuning
+ * run in ms[3] (SMALL, MEDIUM, LARGE; -1 where a shape does not apply).  Any
+ * output pointer may be NULL. */
+int gpl1_batched_tuned(const gpl1_ctx* ctx, int index, long long* key, int* tile, float* ms);
 
 /* Pins the choice for one product shape (shape[5] = {M, N, Kd, Ka, max_splits},
  * as listed by gpl1_gemm_tuned) in the context's cache, so that the solve uses

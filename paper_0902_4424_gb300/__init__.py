@@ -26,6 +26,7 @@ STOP_ON_REL_GAP, STOP_ON_FW = 1, 2
 DEBUG_UNREACHABLE_BARRIER = 1
 ENGINE_AUTO, ENGINE_ONE_READ, ENGINE_TWO_PASS, ENGINE_ONE_READ_NCH2, ENGINE_ONE_READ_NCH4 = 0, 1, 2, 3, 4
 METHOD_GPSS, METHOD_ISTA, METHOD_FISTA, METHOD_PSD = 0, 1, 2, 3
+TILE_AUTO, TILE_SMALL, TILE_MEDIUM, TILE_LARGE = 0, 1, 2, 3
 TRACE_COLS = 28
 # statuses that describe how a solve ended (reported in Result.status, not raised)
 ALGORITHMIC = (0, 3, 4, 5, 6)
@@ -35,7 +36,7 @@ EXPORTS = ["gpl1_create", "gpl1_destroy", "gpl1_set_stream", "gpl1_last_error", 
            "gpl1_gemm_bf16_ex", "gpl1_gemm_tuned", "gpl1_gemm_tuned_set", "gpl1_solve_shared_k", "gpl1_lista_forward",
            "gpl1_lista_grad", "gpl1_lista_train", "gpl1_plan_create", "gpl1_plan_run", "gpl1_plan_destroy",
            "gpl1_solve_async", "gpl1_solve_batched_async", "gpl1_spectral_norm_sq", "gpl1_lista_init",
-           "gpl1_solve_warm", "gpl1_solve_tuned"]
+           "gpl1_solve_warm", "gpl1_solve_tuned", "gpl1_batched_tuned"]
 
 
 class Gpl1Error(RuntimeError):
@@ -51,7 +52,8 @@ class Params(ctypes.Structure):
                 ("stop_rule", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_backtracks", ctypes.c_int),
                 ("alpha0_rule", ctypes.c_int), ("x0_is_zero", ctypes.c_int), ("debug", ctypes.c_int),
                 ("timeout_ns", ctypes.c_longlong), ("engine", ctypes.c_int), ("method", ctypes.c_int),
-                ("lambda_pen", ctypes.c_double), ("step", ctypes.c_double)]
+                ("lambda_pen", ctypes.c_double), ("step", ctypes.c_double), ("tile", ctypes.c_int),
+                ("tile_pad", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -117,6 +119,9 @@ def lib():
         L.gpl1_solve_tuned.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
         L.gpl1_solve_tuned.restype = ctypes.c_int
+        L.gpl1_batched_tuned.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+        L.gpl1_batched_tuned.restype = ctypes.c_int
         L.gpl1_gemm_tuned_set.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
                                           ctypes.c_int]
         L.gpl1_solve_shared_k.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_longlong,
@@ -288,6 +293,18 @@ class Context:
             eng, ms = ctypes.c_int(), ctypes.c_float()
             L.gpl1_solve_tuned(self._h, i, shp, ctypes.byref(eng), ctypes.byref(ms))
             out.append({"shape": tuple(shp), "engine": eng.value, "ms": ms.value})
+        return out
+
+    def batched_tuned(self):
+        """The batched autotuner's choices: [{key: (dtype, count, sum n p, max n p), tile, ms: (S, M, L)}]."""
+        L = lib()
+        count = L.gpl1_batched_tuned(self._h, 0, None, None, None)
+        out = []
+        for i in range(max(count, 0)):
+            key = (ctypes.c_longlong * 4)()
+            tile, ms = ctypes.c_int(), (ctypes.c_float * 3)()
+            L.gpl1_batched_tuned(self._h, i, key, ctypes.byref(tile), ms)
+            out.append({"key": tuple(key), "tile": tile.value, "ms": tuple(ms)})
         return out
 
     def gemm_tuned_set(self, shape, config, splits):

@@ -37,6 +37,13 @@ struct gpl1_ctx {
   size_t aux_bytes = 0;
   // single-solve autotuner: (dtype, n, p, engine class) -> engine and tuned ms
   std::map<std::vector<long long>, std::pair<int, float>> solve_tuned;
+  // batched autotuner: (dtype, count, sum of n p, largest n p, hash of the
+  // shapes) -> tile and the tuning time of each tile (-1: not a candidate)
+  struct TileTune {
+    int tile;
+    float ms[3];
+  };
+  std::map<std::vector<long long>, TileTune> tile_tuned;
 };
 
 namespace {
@@ -65,7 +72,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 int elem_size(int dt) { return dt == GPL1_F64 ? 8 : dt == GPL1_F32 ? 4 : 2; }
 int acc_size(int dt) { return dt == GPL1_F64 ? 8 : 4; }
-int rows_per_box(int dt) { return dt == GPL1_F64 ? Traits<GPL1_F64>::RB : dt == GPL1_F32 ? Traits<GPL1_F32>::RB : Traits<GPL1_BF16>::RB; }
+// rows of a TMA box of the two-pass kernel (the tile's shape)
+int rows_per_box(int dt, int tile = GPL1_TILE_MEDIUM) { return tile_rows(dt, tile); }
 
 gpl1_status ensure_ws(gpl1_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_bytes) return GPL1_OK;
@@ -137,6 +145,8 @@ gpl1_status check_params(gpl1_ctx* ctx, const gpl1_params* p, bool methods = fal
   if (p->alpha0_rule != 0 && p->alpha0_rule != 1) return fail(ctx, GPL1_ERR_INVALID_ARG, "alpha0_rule is 0 or 1");
   if (p->engine < GPL1_ENGINE_AUTO || p->engine > GPL1_ENGINE_ONE_READ_NCH4)
     return fail(ctx, GPL1_ERR_INVALID_ARG, "engine must be one of GPL1_ENGINE_*");
+  if (p->tile < GPL1_TILE_AUTO || p->tile > GPL1_TILE_LARGE)
+    return fail(ctx, GPL1_ERR_INVALID_ARG, "tile must be one of GPL1_TILE_*");
   return GPL1_OK;
 }
 
@@ -215,9 +225,9 @@ struct Sizes {
   int NB, TC;
   long long pp, nn, units;
 };
-Sizes sizes_of(const gpl1_problem* pr, int dt) {
+Sizes sizes_of(const gpl1_problem* pr, int dt, int tile = GPL1_TILE_MEDIUM) {
   Sizes s;
-  const int RB = rows_per_box(dt);
+  const int RB = rows_per_box(dt, tile);
   s.NB = static_cast<int>((pr->n + RB - 1) / RB);
   s.TC = static_cast<int>((pr->p + kBoxCols - 1) / kBoxCols);
   s.pp = static_cast<long long>(s.TC) * kBoxCols;
@@ -329,10 +339,12 @@ struct BatchLayout {
   size_t off_desc = 256, off_res = 0, off_tmap = 0, off_bufs = 0, total = 0;
   std::vector<size_t> off_g, off_k, off_p;
   bool batched = false;
+  int tile = GPL1_TILE_MEDIUM;   // box shape of the launch
 };
 
-BatchLayout batch_layout(const gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt) {
+BatchLayout batch_layout(const gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, int tile) {
   BatchLayout L;
+  L.tile = tile;
   L.order.resize(count);
   std::iota(L.order.begin(), L.order.end(), 0);
   if (count > 1)
@@ -350,7 +362,7 @@ BatchLayout batch_layout(const gpl1_ctx* ctx, const gpl1_problem* probs, int cou
   const int max_group = L.batched ? 1 : ctx->num_sms * 4;
   size_t cur = L.off_bufs;
   for (int q = 0; q < count; ++q) {
-    const Sizes sz = sizes_of(&probs[q], dt);
+    const Sizes sz = sizes_of(&probs[q], dt, tile);
     L.off_g[q] = cur;
     cur = align_up(cur + 3 * sz.pp * as, 256);
     L.off_k[q] = cur;
@@ -395,10 +407,10 @@ gpl1_status stage_batch(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int
     d.pbuf = ws + L.off_p[src];
     gpl1_status st;
     if (L.batched) {
-      st = encode_tmap(ctx, &ht[q], &pr, dt);
+      st = encode_tmap(ctx, &ht[q], &pr, dt, rows_per_box(dt, L.tile));
       d.tmap = ws + L.off_tmap + sizeof(CUtensorMap) * q;
     } else {
-      st = encode_tmap(ctx, tmap0, &pr, dt);
+      st = encode_tmap(ctx, tmap0, &pr, dt, rows_per_box(dt, L.tile));
       d.tmap = nullptr;
     }
     if (st) return st;
@@ -431,22 +443,23 @@ gpl1_status enqueue_batch(gpl1_ctx* ctx, const gpl1_problem* probs, int count, i
   ka.err = reinterpret_cast<int*>(ws + 128);
   ka.prm = to_kernel_params(prm);
   int occ = 0;
-  GPL1_CUDA(cudaFuncSetAttribute(gpss_kernel_ptr(dt), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(gpss_smem_bytes(dt))),
+  GPL1_CUDA(cudaFuncSetAttribute(gpss_kernel_ptr(dt, L.tile), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(gpss_smem_bytes(dt, L.tile))),
             "cudaFuncSetAttribute");
-  GPL1_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gpss_kernel_ptr(dt), kThreads, gpss_smem_bytes(dt)),
+  GPL1_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gpss_kernel_ptr(dt, L.tile), kThreads,
+                                                          gpss_smem_bytes(dt, L.tile)),
             "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (occ < 1) return fail(ctx, GPL1_ERR_CUDA, "solver kernel does not fit on an SM");
   GPL1_CUDA(cudaEventRecordWithFlags(ev0, stream, evf), "cudaEventRecord");
   if (!L.batched) {
-    const Sizes sz = sizes_of(&probs[0], dt);
+    const Sizes sz = sizes_of(&probs[0], dt, L.tile);
     const long long G = std::min<long long>(static_cast<long long>(ctx->num_sms) * occ, sz.units);
     ka.group = static_cast<int>(G);
-    GPL1_CUDA(launch_gpss(dt, ka, tmap0, ka.group, G > 1, stream), "solver launch");
+    GPL1_CUDA(launch_gpss(dt, ka, tmap0, ka.group, G > 1, stream, L.tile), "solver launch");
   } else {
     ka.group = 1;
     const int grid = std::min(ctx->num_sms * occ, count);
-    GPL1_CUDA(launch_gpss(dt, ka, tmap0, grid, false, stream), "solver launch");
+    GPL1_CUDA(launch_gpss(dt, ka, tmap0, grid, false, stream, L.tile), "solver launch");
   }
   GPL1_CUDA(cudaEventRecordWithFlags(ev1, stream, evf), "cudaEventRecord");
   GPL1_CUDA(cudaMemcpyAsync(host_res, ws + L.off_res, sizeof(gpl1_result) * count, res_kind, stream),
@@ -470,9 +483,9 @@ gpl1_status finish_batch(gpl1_ctx* ctx, int count, const gpl1_result* host_res, 
 
 // Enqueue only: the results go to res_dev (device memory), nothing waits.
 gpl1_status run_async(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
-                      gpl1_result* res_dev) {
+                      gpl1_result* res_dev, int tile) {
   GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-  const BatchLayout L = batch_layout(ctx, probs, count, dt);
+  const BatchLayout L = batch_layout(ctx, probs, count, dt, tile);
   gpl1_status st = ensure_ws(ctx, L.total);
   if (st) return st;
   uint8_t* ws = static_cast<uint8_t*>(ctx->ws);
@@ -489,9 +502,9 @@ gpl1_status run_async(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int d
 }
 
 gpl1_status run(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
-                gpl1_result* res) {
+                gpl1_result* res, int tile) {
   GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-  const BatchLayout L = batch_layout(ctx, probs, count, dt);
+  const BatchLayout L = batch_layout(ctx, probs, count, dt, tile);
   gpl1_status st = ensure_ws(ctx, L.total);
   if (st) return st;
   st = ensure_host_res(ctx, count);
@@ -510,6 +523,93 @@ gpl1_status run(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, con
   if (st) return st;
   GPL1_CUDA(cudaStreamSynchronize(ctx->stream), "solver");
   return finish_batch(ctx, count, ctx->host_res, res, ctx->ev[0], ctx->ev[1]);
+}
+
+// The batched autotuner (gpl1_params.tile AUTO): every admissible box shape
+// solves the batch for kTuneIters iterations from x0 = 0 into scratch copies
+// of x, twice; the faster second run wins, per batch (dtype and the list of
+// instance shapes) and context.
+constexpr int kTileTuneIters = 4;
+
+std::vector<long long> tile_key(const gpl1_problem* probs, int count, int dt) {
+  long long sum = 0, mx = 0;
+  unsigned long long h = 1469598103934665603ull;   // FNV-1a over the (n, p) list
+  for (int q = 0; q < count; ++q) {
+    const long long np = probs[q].n * probs[q].p;
+    sum += np;
+    mx = std::max(mx, np);
+    for (long long v : {probs[q].n, probs[q].p})
+      for (int b = 0; b < 8; ++b) {
+        h ^= static_cast<unsigned long long>(v >> (8 * b)) & 0xffull;
+        h *= 1099511628211ull;
+      }
+  }
+  return {dt, count, sum, mx, static_cast<long long>(h & 0x7fffffffffffffffull)};
+}
+
+gpl1_status tune_tile(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
+                      const std::vector<long long>& key, int* best) {
+  const size_t vs = dt == GPL1_F64 ? 8 : 4;
+  std::vector<size_t> off(count);
+  size_t tot = 0;
+  for (int q = 0; q < count; ++q) {
+    off[q] = tot;
+    tot = align_up(tot + static_cast<size_t>(probs[q].p) * vs, 256);
+  }
+  gpl1_status st = ensure_aux(ctx, tot + 256);
+  if (st) return st;
+  std::vector<gpl1_problem> tp(probs, probs + count);
+  for (int q = 0; q < count; ++q) {
+    tp[q].x = static_cast<uint8_t*>(ctx->aux) + off[q];
+    tp[q].trace = nullptr;
+    tp[q].trace_cap = 0;
+  }
+  gpl1_params tq = *prm;
+  tq.stop_rule = 0;
+  tq.max_iter = kTileTuneIters;
+  tq.x0_is_zero = 1;
+  std::vector<gpl1_result> r(count);
+  gpl1_ctx::TileTune rec{GPL1_TILE_MEDIUM, {-1.f, -1.f, -1.f}};
+  float best_ms = 0.f;
+  *best = -1;
+  for (int tl = GPL1_TILE_SMALL; tl <= GPL1_TILE_LARGE; ++tl) {
+    if (!tile_valid(dt, tl)) continue;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      st = run(ctx, tp.data(), count, dt, &tq, r.data(), tl);
+      if (st != GPL1_OK && st != GPL1_ERR_NOT_CONVERGED && st != GPL1_ERR_LINESEARCH) return st;
+      ms = static_cast<float>(r[0].kernel_ms);
+    }
+    rec.ms[tl - GPL1_TILE_SMALL] = ms;
+    if (*best < 0 || ms < best_ms) {
+      *best = tl;
+      best_ms = ms;
+    }
+  }
+  rec.tile = *best;
+  ctx->tile_tuned[key] = rec;
+  return GPL1_OK;
+}
+
+// The box shape of a two-pass launch: the caller's, else MEDIUM for a single
+// instance, else the batched autotuner's choice for this batch.
+gpl1_status pick_tile(gpl1_ctx* ctx, const gpl1_problem* probs, int count, int dt, const gpl1_params* prm,
+                      int* tile) {
+  if (prm->tile != GPL1_TILE_AUTO) {
+    if (!tile_valid(dt, prm->tile)) return fail(ctx, GPL1_ERR_UNSUPPORTED, "tile %d does not apply to this dtype", prm->tile);
+    *tile = prm->tile;
+    return GPL1_OK;
+  }
+  *tile = GPL1_TILE_MEDIUM;
+  if (count < 2) return GPL1_OK;
+  const std::vector<long long> key = tile_key(probs, count, dt);
+  auto it = ctx->tile_tuned.find(key);
+  if (it != ctx->tile_tuned.end()) {
+    *tile = it->second.tile;
+    return GPL1_OK;
+  }
+  GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  return tune_tile(ctx, probs, count, dt, prm, key, tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -660,7 +760,7 @@ gpl1_status tune_engine(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, const gpl
     for (int rep = 0; rep < 2; ++rep) {
       gpl1_result r;
       if (eng == GPL1_ENGINE_TWO_PASS) {
-        st = run(ctx, &tp, 1, dt, &tq, &r);
+        st = run(ctx, &tp, 1, dt, &tq, &r, GPL1_TILE_MEDIUM);
       } else {
         OneRead o;
         if ((st = one_read_choose(ctx, &tp, dt, &o, eng == GPL1_ENGINE_ONE_READ_NCH4 ? 4 : 2))) return st;
@@ -760,7 +860,9 @@ gpl1_status gpl1_solve(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype dt, c
   st = pick_engine(ctx, prob, dt, prm, &o, &one);
   if (st) return st;
   if (one) return run_one_read(ctx, prob, dt, prm, o, res, nullptr);
-  return run(ctx, prob, 1, dt, prm, res);
+  int tile = GPL1_TILE_MEDIUM;
+  if ((st = pick_tile(ctx, prob, 1, dt, prm, &tile))) return st;
+  return run(ctx, prob, 1, dt, prm, res, tile);
 }
 
 gpl1_status gpl1_solve_async(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype dt, const gpl1_params* prm,
@@ -775,7 +877,9 @@ gpl1_status gpl1_solve_async(gpl1_ctx* ctx, const gpl1_problem* prob, gpl1_dtype
   st = pick_engine(ctx, prob, dt, prm, &o, &one);
   if (st) return st;
   if (one) return run_one_read(ctx, prob, dt, prm, o, nullptr, res_dev);
-  return run_async(ctx, prob, 1, dt, prm, res_dev);
+  int tile = GPL1_TILE_MEDIUM;
+  if ((st = pick_tile(ctx, prob, 1, dt, prm, &tile))) return st;
+  return run_async(ctx, prob, 1, dt, prm, res_dev, tile);
 }
 
 gpl1_status gpl1_solve_batched_async(gpl1_ctx* ctx, const gpl1_problem* probs, int count, gpl1_dtype dt,
@@ -789,7 +893,9 @@ gpl1_status gpl1_solve_batched_async(gpl1_ctx* ctx, const gpl1_problem* probs, i
     st = check_problem(ctx, &probs[q], dt, q);
     if (st) return st;
   }
-  return run_async(ctx, probs, count, dt, prm, res_dev);
+  int tile = GPL1_TILE_MEDIUM;
+  if ((st = pick_tile(ctx, probs, count, dt, prm, &tile))) return st;
+  return run_async(ctx, probs, count, dt, prm, res_dev, tile);
 }
 
 gpl1_status gpl1_solve_batched(gpl1_ctx* ctx, const gpl1_problem* probs, int count, gpl1_dtype dt,
@@ -803,7 +909,24 @@ gpl1_status gpl1_solve_batched(gpl1_ctx* ctx, const gpl1_problem* probs, int cou
     st = check_problem(ctx, &probs[q], dt, q);
     if (st) return st;
   }
-  return run(ctx, probs, count, dt, prm, res);
+  int tile = GPL1_TILE_MEDIUM;
+  if ((st = pick_tile(ctx, probs, count, dt, prm, &tile))) return st;
+  return run(ctx, probs, count, dt, prm, res, tile);
+}
+
+int gpl1_batched_tuned(const gpl1_ctx* ctx, int index, long long* key, int* tile, float* ms) {
+  if (!ctx) return -1;
+  const int n = static_cast<int>(ctx->tile_tuned.size());
+  if (index >= 0 && index < n) {
+    auto it = ctx->tile_tuned.begin();
+    std::advance(it, index);
+    if (key)
+      for (int i = 0; i < 4; ++i) key[i] = it->first[i];
+    if (tile) *tile = it->second.tile;
+    if (ms)
+      for (int i = 0; i < 3; ++i) ms[i] = it->second.ms[i];
+  }
+  return n;
 }
 
 }  // extern "C"
@@ -855,6 +978,9 @@ extern "C" gpl1_status gpl1_plan_create(gpl1_ctx* ctx, const gpl1_problem* probs
     if (st) return st;
   }
   GPL1_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  int tile = GPL1_TILE_MEDIUM;
+  st = pick_tile(ctx, probs, count, dt, prm, &tile);
+  if (st) return st;
   gpl1_plan* pl = new gpl1_plan;
   pl->ctx = ctx;
   pl->device = ctx->device;
@@ -862,7 +988,7 @@ extern "C" gpl1_status gpl1_plan_create(gpl1_ctx* ctx, const gpl1_problem* probs
   pl->dt = dt;
   pl->prm = *prm;
   pl->probs.assign(probs, probs + count);
-  pl->layout = batch_layout(ctx, probs, count, dt);
+  pl->layout = batch_layout(ctx, probs, count, dt, tile);
   const BatchLayout& L = pl->layout;
   cudaStream_t cap = nullptr;
   auto bail = [&](gpl1_status code) {
@@ -1028,10 +1154,11 @@ extern "C" gpl1_status gpl1_solve_noalloc(const gpl1_problem* prob, gpl1_dtype d
   host.r.stop = GPL1_STOP_ERROR;
 
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-  const void* fn = gpss_kernel_ptr(dt);
+  const void* fn = gpss_kernel_ptr(dt, GPL1_TILE_MEDIUM);
+  const size_t smem = gpss_smem_bytes(dt, GPL1_TILE_MEDIUM);
   int occ = 0;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(gpss_smem_bytes(dt)));
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, gpss_smem_bytes(dt));
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
   if (e == cudaSuccess && occ < 1) return noalloc_fail(err, err_len, GPL1_ERR_CUDA, "solver kernel does not fit on an SM");
   // zero what the kernel accumulates into: counters, gbuf, kbuf, pbuf; then x0 = 0 if asked
   if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, off_desc, stream);
@@ -1051,7 +1178,7 @@ extern "C" gpl1_status gpl1_solve_noalloc(const gpl1_problem* prob, gpl1_dtype d
   ka.prm = to_kernel_params(prm);
   const long long G = std::min<long long>(static_cast<long long>(num_sms) * occ, s.units);
   ka.group = static_cast<int>(G);
-  e = launch_gpss(dt, ka, tmap, ka.group, G > 1, stream);
+  e = launch_gpss(dt, ka, tmap, ka.group, G > 1, stream, GPL1_TILE_MEDIUM);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&host.r, ws + off_res, sizeof(gpl1_result), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return noalloc_fail(err, err_len, GPL1_ERR_CUDA, cudaGetErrorString(e));

@@ -25,16 +25,15 @@ constexpr int kBoxCols = 256;                 // columns of K per TMA box (one "
 constexpr int kConsumerWarps = 15;            // + 1 producer = 16 warps: 128 registers/thread
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;     // + one TMA producer warp
-constexpr int kStages = 4;                    // depth of the smem ring
-constexpr int kBoxBytes = 30720;              // RB rows x 256 columns, all dtypes
+constexpr int kRingBytes = 122880;            // the two-pass kernel's smem ring (120 KiB, every tile)
 constexpr int kHistBins = 2048;               // radix-select digit of 11 bits
 constexpr int kBinsPerThread = (kHistBins + kConsumers - 1) / kConsumers;
 constexpr int kMaxM = 16;                     // non-monotone memory supported
 constexpr int kMaxMalpha = 8;                 // BB2 window supported
 
 // Storage traits: E = element of K, A = accumulator of products with K,
-// V = element of x and y.  RB = rows per TMA box so a box is 30 KiB and the
-// rows of a box split evenly over the consumer warps.
+// V = element of x and y.  RB = rows per TMA box of the default tile (a box
+// of 30 KiB whose rows split evenly over the consumer warps).
 template <int DT> struct Traits;
 template <> struct Traits<GPL1_F64> {
   using E = double; using A = double; using V = double;
@@ -48,6 +47,29 @@ template <> struct Traits<GPL1_BF16> {
   using E = __nv_bfloat16; using A = float; using V = float;
   static constexpr int ES = 2, RB = 60;
 };
+
+// Box shapes of the two-pass kernel (gpl1_params.tile): a TMA box is RB rows
+// x 256 columns with RB = RPW rows per consumer warp x kConsumerWarps, and the
+// ring holds kRingBytes in every shape:
+//   GPL1_TILE_SMALL   15 KiB boxes, 8 stages (F32: RB 15, BF16: RB 30)
+//   GPL1_TILE_MEDIUM  30 KiB boxes, 4 stages (F64: 15, F32: 30, BF16: 60)
+//   GPL1_TILE_LARGE   60 KiB boxes, 2 stages (F64: 30, F32: 60, BF16: 120)
+// FP64 has no SMALL shape (a warp takes at least one row of a box).
+template <int DT, int TL>
+struct Tile {
+  static constexpr int BOX = 15360 << (TL - GPL1_TILE_SMALL);      // bytes per box
+  static constexpr int STAGES = kRingBytes / BOX;
+  static constexpr int RB = BOX / (kBoxCols * Traits<DT>::ES);      // rows per box
+  static constexpr int RPW = RB / kConsumerWarps;                   // rows per warp
+  static_assert(TL >= GPL1_TILE_SMALL && TL <= GPL1_TILE_LARGE, "tile");
+  static_assert(RPW >= 1 && RPW * kConsumerWarps == RB && RPW <= 8, "rows of a box split over the warps");
+};
+__host__ __device__ constexpr bool tile_valid(int dt, int tl) {
+  return tl >= GPL1_TILE_SMALL && tl <= GPL1_TILE_LARGE && !(dt == GPL1_F64 && tl == GPL1_TILE_SMALL);
+}
+__host__ __device__ constexpr int tile_rows(int dt, int tl) {
+  return (15360 << (tl - GPL1_TILE_SMALL)) / (kBoxCols * (dt == GPL1_F64 ? 8 : dt == GPL1_F32 ? 4 : 2));
+}
 
 // Each lane owns 8 columns of a 256-column strip: NCH 16-byte chunks, chunk m
 // of lane l starting at element (l + 32 m) * EPC.

@@ -18,7 +18,8 @@
 //             f(x + l d) = f_k + l g^T d + l^2 ||K d||^2, so every trial is
 //             scalar work; x_{k+1} = x_k + l d_k; s^T s, s^T z for Alg. SS.
 //
-// Work split.  K is cut into units of RB rows x 256 columns (a 30 KiB TMA box);
+// Work split.  K is cut into units of RB rows x 256 columns (a TMA box of 15,
+// 30 or 60 KiB, the tile; gpl1_params.tile picks it, the batched calls tune it);
 // units are numbered strip-major and each CTA of a group owns one contiguous
 // range.  Pass A walks the range forward, pass B backward, so the tail of
 // pass A is still in L2 when pass B starts on it.  Partial products go to
@@ -153,9 +154,10 @@ struct Uni {
   __device__ void set_gx(double v) { gx_u.d = v; }
 };
 
-template <int DT>
+template <int DT, int TL>
 struct alignas(128) SolverSmem {
-  uint8_t stage[kStages][kBoxBytes];
+  static constexpr int kStages = Tile<DT, TL>::STAGES;
+  uint8_t stage[kStages][Tile<DT, TL>::BOX];
   union {
     typename Traits<DT>::A red[kConsumerWarps][kBoxCols];
     ProjSmem proj;
@@ -224,10 +226,10 @@ struct Dir {
 };
 
 // ------------------------------------------------------------ producer
-template <int DT>
-__device__ void producer_run(const InstDesc& D, const void* tmap, SolverSmem<DT>& sm, uint32_t& it,
+template <int DT, int TL>
+__device__ void producer_run(const InstDesc& D, const void* tmap, SolverSmem<DT, TL>& sm, uint32_t& it,
                              int cta, int G, long long timeout_ns) {
-  constexpr int RB = Traits<DT>::RB;
+  constexpr int RB = Tile<DT, TL>::RB, kStages = Tile<DT, TL>::STAGES, kBoxBytes = Tile<DT, TL>::BOX;
   const int NB = (D.n + RB - 1) / RB, TC = (D.p + kBoxCols - 1) / kBoxCols;
   const long long U = static_cast<long long>(NB) * TC;
   const int u0 = static_cast<int>(U * cta / G), u1 = static_cast<int>(U * (cta + 1) / G);
@@ -263,21 +265,22 @@ done:
 }
 
 // ------------------------------------------------------------ consumers
-template <int DT>
+template <int DT, int TL>
 struct Consumer {
   using T = Traits<DT>;
+  static constexpr int kStages = Tile<DT, TL>::STAGES;
   using A = typename T::A;
   using V = typename T::V;
   using S = typename std::conditional<DT == GPL1_F64, double, F2>::type;   // reduction type
   using LC = LaneCols<DT>;
-  static constexpr int RB = T::RB;
-  static constexpr int RPW = RB / kConsumerWarps;     // rows of a box per warp
+  static constexpr int RB = Tile<DT, TL>::RB;          // rows of a box
+  static constexpr int RPW = Tile<DT, TL>::RPW;        // rows of a box per warp
   static constexpr int VMAX = VMaxOf<DT>::value;      // p <= VMAX * kConsumers
   static constexpr bool kF64 = DT == GPL1_F64;
 
   const KArgs& a;
   const InstDesc& D;
-  SolverSmem<DT>& sm;
+  SolverSmem<DT, TL>& sm;
   uint32_t& it;
   unsigned& epoch;
   const int cta, G, tid, lane, warp, n, p, NB, TC, u0, u1, pp, nn;
@@ -287,7 +290,7 @@ struct Consumer {
   V* x;
   int status = GPL1_OK;
 
-  __device__ Consumer(const KArgs& a_, const InstDesc& D_, SolverSmem<DT>& sm_, uint32_t& it_,
+  __device__ Consumer(const KArgs& a_, const InstDesc& D_, SolverSmem<DT, TL>& sm_, uint32_t& it_,
                       unsigned& ep_, int cta_, int G_)
       : a(a_), D(D_), sm(sm_), it(it_), epoch(ep_), cta(cta_), G(G_), tid(threadIdx.x), lane(threadIdx.x & 31),
         warp(threadIdx.x >> 5), n(D_.n), p(D_.p), NB((D_.n + RB - 1) / RB),
@@ -1357,11 +1360,12 @@ struct Consumer {
   }
 };
 
-template <int DT>
+template <int DT, int TL>
 __global__ void __launch_bounds__(kThreads, 1) gpss_kernel(const __grid_constant__ KArgs a,
                                                            const __grid_constant__ CUtensorMap tmap0) {
+  constexpr int kStages = Tile<DT, TL>::STAGES;
   extern __shared__ uint8_t dyn_smem[];
-  SolverSmem<DT>& sm = *reinterpret_cast<SolverSmem<DT>*>(
+  SolverSmem<DT, TL>& sm = *reinterpret_cast<SolverSmem<DT, TL>*>(
       (reinterpret_cast<uintptr_t>(dyn_smem) + 127) & ~static_cast<uintptr_t>(127));
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -1395,12 +1399,12 @@ __global__ void __launch_bounds__(kThreads, 1) gpss_kernel(const __grid_constant
     const InstDesc& D = a.desc[inst];
     const void* tmap = D.tmap ? D.tmap : static_cast<const void*>(&tmap0);
     if (tid >= kConsumers) {
-      if (tid == kConsumers) producer_run<DT>(D, tmap, sm, it, cta, G, a.prm.timeout_ns);
+      if (tid == kConsumers) producer_run<DT, TL>(D, tmap, sm, it, cta, G, a.prm.timeout_ns);
       // lane 0 of the producer warp ran the producer loop alone: reconverge the
       // warp before the aligned block barrier below
       __syncwarp();
     } else {
-      Consumer<DT> c(a, D, sm, it, epoch, cta, G);
+      Consumer<DT, TL> c(a, D, sm, it, epoch, cta, G);
       c.run();
       __syncwarp();
     }
@@ -1408,5 +1412,46 @@ __global__ void __launch_bounds__(kThreads, 1) gpss_kernel(const __grid_constant
     if (sm.ctl[CTL_BROKEN]) break;   // its barriers are in an unknown state: take no more instances
   }
 }
+
+// Host side of one dtype's kernels (instantiated by gpss_<dtype>.cu): the
+// dynamic shared memory, the kernel and its launch for a tile (GPL1_TILE_*).
+template <int DT, int TL>
+size_t gpss_smem_tl() {
+  return sizeof(SolverSmem<DT, TL>) + 128;
+}
+template <int DT, int TL>
+cudaError_t gpss_launch_tl(const KArgs& a, const CUtensorMap& tmap, int grid, bool cooperative, cudaStream_t stream) {
+  const size_t smem = gpss_smem_tl<DT, TL>();
+  const void* fn = reinterpret_cast<const void*>(gpss_kernel<DT, TL>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<KArgs*>(&a), const_cast<CUtensorMap*>(&tmap)};
+  if (cooperative) return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, smem, stream);
+  return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, stream);
+}
+// tile -> (launch, shared memory, kernel); FP64 has no SMALL tile
+template <int DT>
+struct GpssHost {
+  static constexpr bool kSmall = DT != GPL1_F64;
+  static cudaError_t launch(int tile, const KArgs& a, const CUtensorMap& tmap, int grid, bool coop, cudaStream_t s) {
+    if constexpr (kSmall)
+      if (tile == GPL1_TILE_SMALL) return gpss_launch_tl<DT, GPL1_TILE_SMALL>(a, tmap, grid, coop, s);
+    if (tile == GPL1_TILE_MEDIUM) return gpss_launch_tl<DT, GPL1_TILE_MEDIUM>(a, tmap, grid, coop, s);
+    if (tile == GPL1_TILE_LARGE) return gpss_launch_tl<DT, GPL1_TILE_LARGE>(a, tmap, grid, coop, s);
+    return cudaErrorInvalidValue;
+  }
+  static size_t smem(int tile) {
+    if constexpr (kSmall)
+      if (tile == GPL1_TILE_SMALL) return gpss_smem_tl<DT, GPL1_TILE_SMALL>();
+    if (tile == GPL1_TILE_LARGE) return gpss_smem_tl<DT, GPL1_TILE_LARGE>();
+    return gpss_smem_tl<DT, GPL1_TILE_MEDIUM>();
+  }
+  static const void* kernel(int tile) {
+    if constexpr (kSmall)
+      if (tile == GPL1_TILE_SMALL) return reinterpret_cast<const void*>(gpss_kernel<DT, GPL1_TILE_SMALL>);
+    if (tile == GPL1_TILE_LARGE) return reinterpret_cast<const void*>(gpss_kernel<DT, GPL1_TILE_LARGE>);
+    return reinterpret_cast<const void*>(gpss_kernel<DT, GPL1_TILE_MEDIUM>);
+  }
+};
 
 }  // namespace gpl1

@@ -3,20 +3,11 @@
 
 namespace gpl1 {
 
-cudaError_t launch_gpss_f32(const KArgs& a, const CUtensorMap& tmap, int grid, bool cooperative,
-                              cudaStream_t stream) {
-  const size_t smem = sizeof(SolverSmem<GPL1_F32>) + 128;
-  cudaError_t e = cudaFuncSetAttribute(gpss_kernel<GPL1_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  void* args[] = {const_cast<KArgs*>(&a), const_cast<CUtensorMap*>(&tmap)};
-  if (cooperative)
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(gpss_kernel<GPL1_F32>), dim3(grid),
-                                       dim3(kThreads), args, smem, stream);
-  return cudaLaunchKernel(reinterpret_cast<const void*>(gpss_kernel<GPL1_F32>), dim3(grid), dim3(kThreads),
-                          args, smem, stream);
+cudaError_t launch_gpss_f32(const KArgs& a, const CUtensorMap& tmap, int grid, bool cooperative, cudaStream_t stream,
+                           int tile) {
+  return GpssHost<GPL1_F32>::launch(tile, a, tmap, grid, cooperative, stream);
 }
-size_t gpss_smem_bytes_f32() { return sizeof(SolverSmem<GPL1_F32>) + 128; }
-const void* gpss_kernel_ptr_f32() { return reinterpret_cast<const void*>(gpss_kernel<GPL1_F32>); }
+size_t gpss_smem_bytes_f32(int tile) { return GpssHost<GPL1_F32>::smem(tile); }
+const void* gpss_kernel_ptr_f32(int tile) { return GpssHost<GPL1_F32>::kernel(tile); }
 
 }  // namespace gpl1

@@ -10,12 +10,13 @@
 
 namespace gpl1 {
 
-// Persistent GPSS kernel for element type `dtype` (GPL1_*): grid CTAs of
-// kThreads threads; cooperative launches are used when a group spans CTAs.
+// Persistent GPSS kernel for element type `dtype` (GPL1_*) and box shape
+// `tile` (GPL1_TILE_SMALL / MEDIUM / LARGE, valid for the dtype): grid CTAs
+// of kThreads threads; cooperative launches are used when a group spans CTAs.
 cudaError_t launch_gpss(int dtype, const KArgs& a, const CUtensorMap& tmap, int grid, bool cooperative,
-                        cudaStream_t stream);
-size_t gpss_smem_bytes(int dtype);
-const void* gpss_kernel_ptr(int dtype);
+                        cudaStream_t stream, int tile);
+size_t gpss_smem_bytes(int dtype, int tile);
+const void* gpss_kernel_ptr(int dtype, int tile);
 int gpss_vmax(int dtype);
 
 // Batched projection onto l1 balls, one CTA per segment.

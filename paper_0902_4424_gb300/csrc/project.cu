@@ -94,29 +94,33 @@ cudaError_t launch_project(int dtype, const void* v, void* out, long long p, lon
   return cudaGetLastError();
 }
 
-cudaError_t launch_gpss_f64(const KArgs&, const CUtensorMap&, int, bool, cudaStream_t);
-cudaError_t launch_gpss_f32(const KArgs&, const CUtensorMap&, int, bool, cudaStream_t);
-cudaError_t launch_gpss_bf16(const KArgs&, const CUtensorMap&, int, bool, cudaStream_t);
-size_t gpss_smem_bytes_f64();
-size_t gpss_smem_bytes_f32();
-size_t gpss_smem_bytes_bf16();
-const void* gpss_kernel_ptr_f64();
-const void* gpss_kernel_ptr_f32();
-const void* gpss_kernel_ptr_bf16();
+cudaError_t launch_gpss_f64(const KArgs&, const CUtensorMap&, int, bool, cudaStream_t, int);
+cudaError_t launch_gpss_f32(const KArgs&, const CUtensorMap&, int, bool, cudaStream_t, int);
+cudaError_t launch_gpss_bf16(const KArgs&, const CUtensorMap&, int, bool, cudaStream_t, int);
+size_t gpss_smem_bytes_f64(int);
+size_t gpss_smem_bytes_f32(int);
+size_t gpss_smem_bytes_bf16(int);
+const void* gpss_kernel_ptr_f64(int);
+const void* gpss_kernel_ptr_f32(int);
+const void* gpss_kernel_ptr_bf16(int);
 
 cudaError_t launch_gpss(int dtype, const KArgs& a, const CUtensorMap& tmap, int grid, bool cooperative,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, int tile) {
   switch (dtype) {
-    case GPL1_F64: return launch_gpss_f64(a, tmap, grid, cooperative, stream);
-    case GPL1_F32: return launch_gpss_f32(a, tmap, grid, cooperative, stream);
-    default: return launch_gpss_bf16(a, tmap, grid, cooperative, stream);
+    case GPL1_F64: return launch_gpss_f64(a, tmap, grid, cooperative, stream, tile);
+    case GPL1_F32: return launch_gpss_f32(a, tmap, grid, cooperative, stream, tile);
+    default: return launch_gpss_bf16(a, tmap, grid, cooperative, stream, tile);
   }
 }
-size_t gpss_smem_bytes(int dtype) {
-  return dtype == GPL1_F64 ? gpss_smem_bytes_f64() : dtype == GPL1_F32 ? gpss_smem_bytes_f32() : gpss_smem_bytes_bf16();
+size_t gpss_smem_bytes(int dtype, int tile) {
+  return dtype == GPL1_F64 ? gpss_smem_bytes_f64(tile)
+         : dtype == GPL1_F32 ? gpss_smem_bytes_f32(tile)
+                             : gpss_smem_bytes_bf16(tile);
 }
-const void* gpss_kernel_ptr(int dtype) {
-  return dtype == GPL1_F64 ? gpss_kernel_ptr_f64() : dtype == GPL1_F32 ? gpss_kernel_ptr_f32() : gpss_kernel_ptr_bf16();
+const void* gpss_kernel_ptr(int dtype, int tile) {
+  return dtype == GPL1_F64 ? gpss_kernel_ptr_f64(tile)
+         : dtype == GPL1_F32 ? gpss_kernel_ptr_f32(tile)
+                             : gpss_kernel_ptr_bf16(tile);
 }
 int gpss_vmax(int dtype) {
   return dtype == GPL1_F64 ? VMaxOf<GPL1_F64>::value : dtype == GPL1_F32 ? VMaxOf<GPL1_F32>::value

@@ -46,8 +46,8 @@ def test_struct_layouts_match_header(tmp_path):
 #include "{HEADER}"
 int main(void) {{
   printf("%zu %zu %zu\\n", sizeof(gpl1_params), sizeof(gpl1_result), sizeof(gpl1_problem));
-  printf("%zu %zu %zu %zu %zu\\n", offsetof(gpl1_params, timeout_ns), offsetof(gpl1_result, fail_iter), offsetof(gpl1_problem, trace_cap),
-         offsetof(gpl1_params, method), offsetof(gpl1_params, step));
+  printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(gpl1_params, timeout_ns), offsetof(gpl1_result, fail_iter), offsetof(gpl1_problem, trace_cap),
+         offsetof(gpl1_params, method), offsetof(gpl1_params, step), offsetof(gpl1_params, tile));
   return 0;
 }}''')
     exe = tmp_path / "sz"
@@ -57,7 +57,7 @@ int main(void) {{
                                            ctypes.sizeof(pkg.Problem)]
     assert [int(v) for v in b.split()] == [pkg.Params.timeout_ns.offset, pkg.Result.fail_iter.offset,
                                            pkg.Problem.trace_cap.offset, pkg.Params.method.offset,
-                                           pkg.Params.step.offset]
+                                           pkg.Params.step.offset, pkg.Params.tile.offset]
 
 
 def test_null_context_is_rejected_without_a_gpu():
@@ -67,3 +67,17 @@ def test_null_context_is_rejected_without_a_gpu():
     res = pkg.Result()
     assert L.gpl1_solve(None, None, 1, ctypes.byref(prm), ctypes.byref(res)) == 1
     assert L.gpl1_project(None, None, None, 1, 10, 1, 10, None, 0, None) == 1
+
+
+def test_parameter_checks_run_before_any_device_call():
+    """gpl1_solve_noalloc checks its parameters on the host before it touches a
+    device, so the refusals are visible without a GPU: an engine or tile out of
+    range, and the comparison methods (single solves only)."""
+    L = pkg.lib()
+    res = pkg.Result()
+    err = ctypes.create_string_buffer(256)
+    for over, word in (({"tile": 4}, b"tile"), ({"tile": -1}, b"tile"), ({"engine": 9}, b"engine"),
+                       ({"method": pkg.METHOD_FISTA}, b"ISTA")):
+        prm = pkg.params_default(**over)
+        st = L.gpl1_solve_noalloc(None, 1, ctypes.byref(prm), ctypes.byref(res), None, err, 256)
+        assert st in (1, 7) and word in err.value, (over, st, err.value)
