@@ -360,6 +360,7 @@ def run_shared_k(nrhs, dev, verify=16, plain=8, pin=None):
     plain_ms = t0.elapsed_time(t1) / plain
     # executed tensor-core work: per iteration 2 p nrhs 3n (K^T R) + 2 n nrhs 3p (K D)
     flops = 12.0 * n * p * nrhs * max(iters)
+    method_flops = 4.0 * n * p * sum(iters)
     tuned = [{"shape_MNKdKa": list(t["shape"][:4]), "config": t["config"], "splits": t["splits"],
               "ms": round(t["ms"], 4)} for t in ctx.gemm_tuned()]
     peaks_d = {}
@@ -378,6 +379,11 @@ def run_shared_k(nrhs, dev, verify=16, plain=8, pin=None):
            "verified_max_rel_gap": max(gaps), "verified_instances": len(gaps),
            "tensor_tflops": flops / (ms / 1e3) / 1e12,
            "tensor_frac_of_measured_bf16": flops / (ms / 1e3) / 1e12 / tf_peak,
+           # the method's own products (2 n p for K^T r, 2 n p for K d, per
+           # instance and iteration it ran), without the split of the vector operand
+           "method_tflops": method_flops / (ms / 1e3) / 1e12,
+           "method_frac_of_measured_bf16": method_flops / (ms / 1e3) / 1e12 / tf_peak,
+           "ms_per_iteration": ms / max(iters),
            "gemm_autotuned": tuned,
            "note": "executed GEMM work incl. the 3-term BF16 split of the vector operand; all iterations of the call"}
     ctx.close()
