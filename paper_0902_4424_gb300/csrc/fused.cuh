@@ -876,20 +876,40 @@ struct FC {
         float vals[2 * R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-          float pd = 0.f, px = 0.f;
+          if constexpr (DT == GPL1_F32) {
+            // even and odd columns in the two halves of packed FP32 FMAs
+            float2 pd = make_float2(0.f, 0.f), px = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int m = 0; m < NCH; ++m) {
-            if (!cv[m]) continue;
-            A kv[EPC];
-            widen16<DT>(stg + soff[m] + q * kBoxW * ES, kv);
+            for (int m = 0; m < NCH; ++m) {
+              if (!cv[m]) continue;
+              A kv[EPC];
+              widen16<DT>(stg + soff[m] + q * kBoxW * ES, kv);
 #pragma unroll
-            for (int e = 0; e < EPC; ++e) {
-              pd = fmaf(kv[e], d[m * EPC + e], pd);
-              px = fmaf(kv[e], x[m * EPC + e], px);
+              for (int e = 0; e < EPC; e += 2) {
+                const int j = m * EPC + e;
+                const float2 k2 = make_float2(kv[e], kv[e + 1]);
+                pd = __ffma2_rn(k2, make_float2(d[j], d[j + 1]), pd);
+                px = __ffma2_rn(k2, make_float2(x[j], x[j + 1]), px);
+              }
             }
+            vals[2 * q] = pd.x + pd.y;
+            vals[2 * q + 1] = px.x + px.y;
+          } else {
+            float pd = 0.f, px = 0.f;
+#pragma unroll
+            for (int m = 0; m < NCH; ++m) {
+              if (!cv[m]) continue;
+              A kv[EPC];
+              widen16<DT>(stg + soff[m] + q * kBoxW * ES, kv);
+#pragma unroll
+              for (int e = 0; e < EPC; ++e) {
+                pd = fmaf(kv[e], d[m * EPC + e], pd);
+                px = fmaf(kv[e], x[m * EPC + e], px);
+              }
+            }
+            vals[2 * q] = pd;
+            vals[2 * q + 1] = px;
           }
-          vals[2 * q] = pd;
-          vals[2 * q + 1] = px;
         }
         const float tot = warp_sum_many<2 * R>(vals, lane);
         constexpr int GL = 32 / (2 * R);
@@ -1156,15 +1176,40 @@ struct FC {
             const uint8_t* stg = sm.stage[st];
 #pragma unroll
             for (int qq = 0; qq < R; ++qq) {
+              if constexpr (DT == GPL1_F32) {
+                // two columns per instruction (packed FP32 FMA; each half is
+                // the same rounded fma as the scalar form)
+                const float2 w1 = make_float2(m1[qq], m1[qq]), w2 = make_float2(m2[qq], m2[qq]);
 #pragma unroll
-              for (int mm = 0; mm < NCH; ++mm) {
-                if (!cv[mm]) continue;
-                A kv[EPC];
-                widen16<DT>(stg + soff[mm] + qq * kBoxW * ES, kv);
+                for (int mm = 0; mm < NCH; ++mm) {
+                  if (!cv[mm]) continue;
+                  A kv[EPC];
+                  widen16<DT>(stg + soff[mm] + qq * kBoxW * ES, kv);
 #pragma unroll
-                for (int e = 0; e < EPC; ++e) {
-                  u1[mm * EPC + e] = vfma(kv[e], m1[qq], u1[mm * EPC + e]);
-                  if constexpr (!SETUP) u2[mm * EPC + e] = vfma(kv[e], m2[qq], u2[mm * EPC + e]);
+                  for (int e = 0; e < EPC; e += 2) {
+                    const int j = mm * EPC + e;
+                    const float2 k2 = make_float2(kv[e], kv[e + 1]);
+                    const float2 a1 = __ffma2_rn(k2, w1, make_float2(u1[j], u1[j + 1]));
+                    u1[j] = a1.x;
+                    u1[j + 1] = a1.y;
+                    if constexpr (!SETUP) {
+                      const float2 a2 = __ffma2_rn(k2, w2, make_float2(u2[j], u2[j + 1]));
+                      u2[j] = a2.x;
+                      u2[j + 1] = a2.y;
+                    }
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int mm = 0; mm < NCH; ++mm) {
+                  if (!cv[mm]) continue;
+                  A kv[EPC];
+                  widen16<DT>(stg + soff[mm] + qq * kBoxW * ES, kv);
+#pragma unroll
+                  for (int e = 0; e < EPC; ++e) {
+                    u1[mm * EPC + e] = vfma(kv[e], m1[qq], u1[mm * EPC + e]);
+                    if constexpr (!SETUP) u2[mm * EPC + e] = vfma(kv[e], m2[qq], u2[mm * EPC + e]);
+                  }
                 }
               }
             }
