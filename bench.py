@@ -704,12 +704,23 @@ def run_ours(args, rank, world, local_rank):
     kms = statistics.mean(kernel_ms)
     achieved = algo_bytes / (kms / 1e3) / 1e9
     peak, peak_kind = peaks()
+    # the kernel that ran the timed solves: the autotuner's choice for this shape,
+    # or the engine pinned on the command line
+    labels = {pkg.ENGINE_ONE_READ_NCH2: "gpl1::fz::fused_kernel<1,2> (one-read engine, two column chunks per thread)",
+              pkg.ENGINE_ONE_READ_NCH4: "gpl1::fz::fused_kernel<1,4> (one-read engine, four column chunks per thread)",
+              pkg.ENGINE_TWO_PASS: "gpl1::gpss_kernel<1,2> (two-pass engine)"}
+    ran = engine
+    for t in ctx.solve_tuned():
+        if t["shape"][1] == n and t["shape"][2] == p and engine in (pkg.ENGINE_AUTO, pkg.ENGINE_ONE_READ):
+            ran = t["engine"]
+    kernel_label = labels.get(ran, str(ran))
     traffic = None
     tr_file = os.path.join(ROOT, "profiles", "fused_kernel_c1_f32_traffic.txt")   # JSON text
     if os.path.exists(tr_file):
         with open(tr_file) as fh:
             tr = json.load(fh)
-        if tr.get("workload") == prob.name and tr.get("kernel_fingerprint") == kernel_fingerprint():
+        if (tr.get("workload") == prob.name and tr.get("kernel_fingerprint") == kernel_fingerprint()
+                and kernel_label.startswith(tr.get("kernel", "?"))):
             traffic = tr.get("dram_bytes_per_launch")
 
     # ---- CPU baseline: the oracle on this host's cores, one bounded sample
@@ -736,7 +747,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "frac_of_nominal_8tbs": achieved / 8000.0,
-                     "kernel": "gpl1::fz::fused_kernel<1,2> (one-read engine, two column chunks per thread)",
+                     "kernel": kernel_label,
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "algorithmic_bytes": "one read of K (n p 4 B) per pass; passes = iterations + 1",
                      "kernel_ms": kms},
@@ -794,7 +805,7 @@ def run_engine_compare(ctx, K, y, prob, prm, flush, steps, dev):
     kms = statistics.mean(r.kernel_ms for r in res)
     algo = 2.0 * prob.n * prob.p * prob.K.itemsize * iters
     peak, _ = peaks()
-    return {"kernel": "gpl1::gpss_kernel<1> (two-pass engine)", "solves_per_s": 1e3 / statistics.mean(ms),
+    return {"kernel": "gpl1::gpss_kernel<1,2> (two-pass engine, 30 KiB boxes)", "solves_per_s": 1e3 / statistics.mean(ms),
             "ms_per_solve": statistics.mean(ms), "iters_per_solve": iters, "kernel_ms": kms,
             "hbm_gbs": algo / (kms / 1e3) / 1e9, "roofline_frac": algo / (kms / 1e3) / 1e9 / peak,
             "algorithmic_bytes": "two reads of K per iteration", "ok": sum(r.status == 0 for r in res)}

@@ -876,7 +876,7 @@ struct FC {
         float vals[2 * R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-          if constexpr (DT == GPL1_F32) {
+          if constexpr (!kF64) {
             // even and odd columns in the two halves of packed FP32 FMAs
             float2 pd = make_float2(0.f, 0.f), px = make_float2(0.f, 0.f);
 #pragma unroll
@@ -1176,7 +1176,7 @@ struct FC {
             const uint8_t* stg = sm.stage[st];
 #pragma unroll
             for (int qq = 0; qq < R; ++qq) {
-              if constexpr (DT == GPL1_F32) {
+              if constexpr (!kF64) {
                 // two columns per instruction (packed FP32 FMA; each half is
                 // the same rounded fma as the scalar form)
                 const float2 w1 = make_float2(m1[qq], m1[qq]), w2 = make_float2(m2[qq], m2[qq]);
