@@ -40,14 +40,6 @@ METRIC = "solves/sec to rel. objective gap 1e-6 (batched+warm vs plain GP); HBM 
 TOL = 1e-6
 
 
-def load_baseline_metric():
-    try:
-        with open(os.path.join(ROOT, "BASELINE.json")) as fh:
-            return json.load(fh).get("metric", METRIC)
-    except OSError:
-        return METRIC
-
-
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -167,7 +159,7 @@ def run_reference(args, rank, world):
     value = args.steps / total
     sample = f"{args.steps} full oracle solves of {prob.name} to rel gap {TOL:g} ({statistics.mean(iters):.0f} iterations each)"
     line = {
-        "impl": "reference", "metric": load_baseline_metric(), "value": value, "unit": "solves/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": prob.name, "n": prob.n, "p": prob.p, "stop": f"rel_gap<={TOL:g} vs oracle f*"},
@@ -732,7 +724,7 @@ def run_ours(args, rank, world, local_rank):
                          f"({statistics.mean(oit):.0f} iterations each), {sum(times):.1f} s"}
 
     line = {
-        "metric": load_baseline_metric(), "value": value, "unit": "solves/s", "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": prob.name, "n": n, "p": p, "rho": prob.rho, "stop": f"rel_gap<={TOL:g} vs oracle f*",
@@ -985,7 +977,7 @@ def main():
         torch.cuda.set_device(local_rank)
         out = run_batched(512, max(1, args.steps // 20), torch.device("cuda", local_rank))
         if rank == 0:
-            print(json.dumps({"metric": load_baseline_metric(), "value": out["solves_per_s"], "unit": "solves/s",
+            print(json.dumps({"metric": METRIC, "value": out["solves_per_s"], "unit": "solves/s",
                               "n_gpus": world, "steps": max(1, args.steps // 20), "warmup": 2,
                               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
                               "data": "synthetic", "config": {"workload": out["workload"]}, "batched": out}),

@@ -47,7 +47,7 @@ typedef enum {
   GPL1_ERR_LINESEARCH = 4,    /* Armijo backtracking cap reached (Alg. GP, Step 5)  */
   GPL1_ERR_NONFINITE = 5,     /* f, a dot product or the steplength became NaN/inf  */
   GPL1_ERR_TIMEOUT = 6,       /* a device-side wait exceeded timeout_ns             */
-  GPL1_ERR_UNSUPPORTED = 7    /* size beyond what this build handles                */
+  GPL1_ERR_UNSUPPORTED = 7    /* size or shape beyond what the library handles      */
 } gpl1_status;
 
 typedef enum { GPL1_F64 = 0, GPL1_F32 = 1, GPL1_BF16 = 2 } gpl1_dtype;

@@ -39,14 +39,14 @@ import oracle  # noqa: E402
 import workloads as W  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fstar.json")
-CONFIGS = {"c0": W.config0, "c1": W.config1, "c2": W.config2}
+WORKLOAD_OF = {"c0": W.config0, "c1": W.config1, "c2": W.config2}
 
 
 def main(names):
     gold = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for name in names:
         t = time.time()
-        prob = CONFIGS[name]()
+        prob = WORKLOAD_OF[name]()
         x, res, _ = oracle.reference_solve(prob)
         gold[name] = {
             "workload": prob.name, "n": prob.n, "p": prob.p, "rho": prob.rho,
@@ -159,8 +159,8 @@ def main_xstar(which=("c0", "c1", "c2", "c3a", "c3b", "c4", "c5")):
     gold = json.load(open(OUT))
     for name in which:
         t = time.time()
-        if name in CONFIGS:
-            prob = CONFIGS[name]()
+        if name in WORKLOAD_OF:
+            prob = WORKLOAD_OF[name]()
             x, res, _ = oracle.reference_solve(prob)
             meta = {"workload": prob.name, "f": res.f, "f_star_file": gold[name]["f_star"], "solver": "oracle.reference_solve"}
             _save_sparse(os.path.join(d, f"xstar_{name}.npz"), [x], meta)
@@ -285,4 +285,4 @@ if __name__ == "__main__":
     elif args == ["c3b"]:
         main_c3b()
     else:
-        main(args or list(CONFIGS))
+        main(args or list(WORKLOAD_OF))
