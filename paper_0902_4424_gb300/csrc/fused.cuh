@@ -65,7 +65,7 @@ constexpr int kStageBytes = 32768;      // one row block of one CTA's slice
 constexpr int kBoxW = 256;              // TMA box width (elements)
 constexpr int kCMax = 16;               // CTAs per cluster
 constexpr int kCB = 4;                  // row blocks per chunk (one row-sum exchange per chunk)
-constexpr int kLagC = 3;                // chunks between a chunk's row sums and its K^T step
+constexpr int kLagC = 2;                // chunks between a chunk's row sums and its K^T step (3: 2.4 % slower on c1, 1: 17 %)
 constexpr int kNRed = kLagC + 1;        // chunk slots of the warp partials
 constexpr int kRNS = 6;                 // chunk slots of the row-sum channel (> kLagC + 1)
 constexpr int kNTot = 3;                // chunk slots of the published row multipliers
