@@ -622,7 +622,7 @@ struct OneRead {
 };
 
 // Chunks per thread and cluster size for p columns (the smallest cluster that
-// covers p with one chunk per thread, else with two; portable sizes first),
+// covers p with two chunks per thread, else with four; portable sizes first),
 // and the number of clusters that stay resident together.
 gpl1_status one_read_choose(gpl1_ctx* ctx, const gpl1_problem* pr, int dt, OneRead* o, int want_nch = 0) {
   const long long p = pr->p;

@@ -17,16 +17,18 @@
 //     CTA rank r of every cluster owns the column slice [r W, r W + W), so the
 //     C CTAs of a cluster together cover all p columns and every cluster holds
 //     one copy of x, d and g, distributed over its CTAs.
-//   * Thread t of a CTA owns NCH 16-byte chunks of the slice (chunk t + 512 m)
+//   * Thread t of a CTA owns NCH 16-byte chunks of the slice (chunk t + 256 m)
 //     and keeps x, d, g and the two gradient accumulators of its columns in
 //     registers for the whole solve.
 //   * A row block arrives through TMA (boxes of 256 columns x R rows).  Each
-//     thread forms its partial row sums, the 8 warps reduce them, and warp 0
-//     sends the CTA's partials of the block to every CTA of the cluster through
-//     distributed shared memory (st.async with an mbarrier transaction count).
-//     Every CTA adds the C partials in rank order, so all CTAs of a cluster
-//     hold bit-identical row sums, then accumulates K_i^T of the block into
-//     its columns.  The exchange of block b overlaps the accumulation of b-1.
+//     thread forms its partial row sums, each consumer warp reduces them, the
+//     sender warp adds the CTA's partials of a chunk of blocks and sends them
+//     to every CTA of the cluster through distributed shared memory (bulk
+//     copies with an mbarrier transaction count), and the totaler warp adds
+//     the C messages in rank order, so all CTAs of a cluster hold
+//     bit-identical row sums.  kLagC chunks later the same blocks arrive again
+//     (from L2) and each thread accumulates K_i^T of them into its columns, so
+//     the exchange of a chunk overlaps the next chunks' work.
 //   * At the end of the pass every CTA adds its gradient accumulators into a
 //     global buffer (vector reductions at L2) and its scalar partials into a
 //     per-CTA record; one grid barrier follows.
