@@ -186,6 +186,20 @@ def whole_job_rate(world: int, steps: int, max_total_ms: float) -> float:
     return world * steps / (max_total_ms / 1e3)
 
 
+def lpt_partition(costs, world: int):
+    """Instances to ranks by longest processing time first: in decreasing cost,
+    each instance goes to the rank with the least work so far (ties to the
+    lower rank).  Every rank computes the same partition from the same costs."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    loads = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (loads[k], k))
+        parts[r].append(i)
+        loads[r] += costs[i]
+    return parts
+
+
 def objective_f64(prob, x) -> float:
     """f(x) = ||K x - y||^2 in FP64 on the stored K (numpy; a check of the returned
     x against the stored optimum, outside every timed region)."""
@@ -300,6 +314,70 @@ def run_batched(count, steps, dev, plain_sample=64):
     out["tile_pinned"] = pinned
     ctx.close()
     return out
+
+
+def run_batched_sharded(rank, world, steps, warmup, dev, count=512):
+    """The 512 ragged instances shared out over the ranks by LPT on n p (no
+    collective on the data path: each rank solves its share with one batched
+    launch per step); the whole job's rate is count instances per step over the
+    slowest rank's time (total work fixed: strong scaling).  Rank 0 prints."""
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+
+    import paper_0902_4424_gb300 as pkg
+    import workloads as W
+    sizes = W.ragged_sizes(512)[:count]
+    share = lpt_partition([4.0 * n * n for n in sizes], world)[rank]
+    with open(os.path.join(ROOT, "tests", "golden", "c3a_fstar.json")) as fh:
+        fstars = json.load(fh)["f_star"][:count]
+    probs, keep, descs = [], [], []
+    for i in share:
+        pr = W.ragged_instance(i, sizes[i])
+        K = torch.from_numpy(pr.K.view(np.int16)).to(dev)
+        y = torch.from_numpy(pr.y).to(dev)
+        x = torch.zeros(pr.p, dtype=torch.float32, device=dev)
+        probs.append(pr)
+        keep.append((K, y, x))
+        descs.append(pkg.Context.make_problem(K, y, pr.rho, x, pr.p, fstars[i]))
+    ctx = pkg.Context(dev.index or 0)
+    prm = pkg.params_default(stop_rule=pkg.STOP_ON_REL_GAP, tol=0.5 * TOL, x0_is_zero=1, max_iter=20000)
+    for _ in range(warmup):
+        ctx.solve_batched(descs, pkg.BF16, prm)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    a.record(stream)
+    ok = 0
+    for _ in range(steps):
+        res = ctx.solve_batched(descs, pkg.BF16, prm)
+        ok = sum(r.status == 0 for r in res)
+    b.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    mine = a.elapsed_time(b)
+    mx = max_over_ranks(mine, world, dev)
+    gaps = [(objective_f64(pr, k[2].double().cpu().numpy()) - fstars[i]) / fstars[i]
+            for pr, k, i in list(zip(probs, keep, share))[:8]]
+    worst = max_over_ranks(max(gaps) if gaps else 0.0, world, dev)
+    ok_all = max_over_ranks(float(len(share) - ok), world, dev)   # the most instances any rank left unsolved
+    value = count * steps / (mx / 1e3)
+    if rank == 0:
+        loads = [sum(4.0 * sizes[i] ** 2 for i in part) for part in lpt_partition([4.0 * n * n for n in sizes], world)]
+        print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": steps,
+                          "warmup": warmup, "ms_per_step": mx / steps, "higher_is_better": True, "scaling": "strong",
+                          "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                          "config": {"workload": f"c3a_ragged{count}_bf16", "parallelism": f"lpt over {world} ranks",
+                                     "l2": "each step solves every instance of the share from x0 = 0"},
+                          "shares": [len(p) for p in lpt_partition([4.0 * n * n for n in sizes], world)],
+                          "load_imbalance": max(loads) / (sum(loads) / world),
+                          "unsolved_max_per_rank": ok_all, "verified_max_rel_gap": worst,
+                          "gpu_launches": steps}), flush=True)
+    ctx.close()
 
 
 # ------------------------------------------------ shared-K form (c3b)
@@ -976,6 +1054,11 @@ def main():
             dist.init_process_group("gloo")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "c3a" and world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        run_batched_sharded(rank, world, max(1, args.steps // 20), max(args.warmup, 3),
+                            torch.device("cuda", local_rank))
     elif args.workload == "c3a":
         import torch
         torch.cuda.set_device(local_rank)

@@ -62,3 +62,23 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(12.5, 1) == 12.5
     assert bench.whole_job_rate(1, 4, 100.0) == pytest.approx(40.0)
+
+
+def test_lpt_partition_of_the_ragged_batch():
+    """The ragged batch's instances shared out over ranks (bench --workload c3a
+    under torchrun): every instance on exactly one rank, the same partition on
+    every rank, and no rank above the mean load by more than the largest
+    instance (the LPT bound)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    sizes = W.ragged_sizes(512)
+    costs = [4.0 * n * n for n in sizes]
+    for world in (1, 2, 3, 4, 8):
+        parts = bench.lpt_partition(costs, world)
+        assert parts == bench.lpt_partition(costs, world)
+        flat = sorted(i for part in parts for i in part)
+        assert flat == list(range(len(sizes)))
+        loads = [sum(costs[i] for i in part) for part in parts]
+        assert max(loads) <= sum(costs) / world + max(costs)
+        assert all(len(part) > 0 for part in parts)
