@@ -59,17 +59,19 @@ constexpr int kThr = kCons + 96;        // + TMA producer warp, sender warp, tot
 constexpr int kProd = kCons;            // first thread of the producer warp
 constexpr int kSend = kCons + 32;       // ... of the sender warp
 constexpr int kTot = kCons + 64;        // ... of the totaler warp
-constexpr int kNSA = 3;                 // stages of the ring that streams K from HBM (A steps)
-constexpr int kNSB = 2;                 // stages of the ring that re-reads blocks from L2 (B steps)
+constexpr int kNSA = 2;                 // stages of the ring that streams K from HBM (A steps)
+constexpr int kNSB = 1;                 // stages of the ring that re-reads blocks from L2 (B steps)
 constexpr int kNST = kNSA + kNSB;
 constexpr int CTL_ISSUED_B = 7;         // (sm.ctl) loads issued into the B ring
-constexpr int kStageBytes = 32768;      // one row block of one CTA's slice
+constexpr int kStageBytes = 65536;      // one row block of one CTA's slice (8 rows FP32: taller blocks
+                                        // halve the per-block waits and reductions; 3.50 against 3.89 ms
+                                        // on c1 with 4-row blocks in a 3 + 2 stage ring)
 constexpr int kBoxW = 256;              // TMA box width (elements)
 constexpr int kCMax = 16;               // CTAs per cluster
-constexpr int kCB = 4;                  // row blocks per chunk (one row-sum exchange per chunk)
+constexpr int kCB = 2;                  // row blocks per chunk (one row-sum exchange per chunk)
 constexpr int kLagC = 2;                // chunks between a chunk's row sums and its K^T step (3: 2.4 % slower on c1, 1: 17 %)
 constexpr int kNRed = kLagC + 1;        // chunk slots of the warp partials
-constexpr int kRNS = 6;                 // chunk slots of the row-sum channel (> kLagC + 1)
+constexpr int kRNS = 5;                 // chunk slots of the row-sum channel (> kLagC + 1)
 constexpr int kNTot = 3;                // chunk slots of the published row multipliers
 constexpr int kRCW = 64;                // words per CTA of one chunk's row sums (at most)
 constexpr uint32_t kSleepNs = 20000;    // suspend hint of a blocking mbarrier wait
