@@ -44,9 +44,15 @@ cudaError_t prepare(const void* fn, size_t smem) {
 }  // namespace
 
 int fused_rows(int dt, int nch) {
-  const int es = dt == GPL1_F64 ? 8 : dt == GPL1_F32 ? 4 : 2;
-  const int w = fz::kCons * (16 / es) * nch;
-  return fz::kStageBytes / (w * es);
+  switch (dt * 8 + nch) {
+    case GPL1_F64 * 8 + 2: return fz::Cfg<GPL1_F64, 2>::R;
+    case GPL1_F64 * 8 + 4: return fz::Cfg<GPL1_F64, 4>::R;
+    case GPL1_F32 * 8 + 2: return fz::Cfg<GPL1_F32, 2>::R;
+    case GPL1_F32 * 8 + 4: return fz::Cfg<GPL1_F32, 4>::R;
+    case GPL1_BF16 * 8 + 2: return fz::Cfg<GPL1_BF16, 2>::R;
+    case GPL1_BF16 * 8 + 4: return fz::Cfg<GPL1_BF16, 4>::R;
+    default: return 0;
+  }
 }
 int fused_width(int dt, int nch) {
   const int es = dt == GPL1_F64 ? 8 : dt == GPL1_F32 ? 4 : 2;

@@ -59,16 +59,14 @@ constexpr int kThr = kCons + 96;        // + TMA producer warp, sender warp, tot
 constexpr int kProd = kCons;            // first thread of the producer warp
 constexpr int kSend = kCons + 32;       // ... of the sender warp
 constexpr int kTot = kCons + 64;        // ... of the totaler warp
-constexpr int kNSA = 2;                 // stages of the ring that streams K from HBM (A steps)
-constexpr int kNSB = 1;                 // stages of the ring that re-reads blocks from L2 (B steps)
-constexpr int kNST = kNSA + kNSB;
+// The ring shape (stages, row-block bytes, blocks per chunk) is per dtype: see
+// Cfg.  Float data: row blocks of 64 KB per CTA (8 rows FP32) through two HBM
+// stages and one L2 stage; taller blocks halve the per-block waits and
+// reductions (3.50 against 3.89 ms on c1 with 4-row blocks in a 3 + 2 ring).
+// FP64 data (c0-sized, latency-bound solves): 32 KB blocks in a 3 + 2 ring.
 constexpr int CTL_ISSUED_B = 7;         // (sm.ctl) loads issued into the B ring
-constexpr int kStageBytes = 65536;      // one row block of one CTA's slice (8 rows FP32: taller blocks
-                                        // halve the per-block waits and reductions; 3.50 against 3.89 ms
-                                        // on c1 with 4-row blocks in a 3 + 2 stage ring)
 constexpr int kBoxW = 256;              // TMA box width (elements)
 constexpr int kCMax = 16;               // CTAs per cluster
-constexpr int kCB = 2;                  // row blocks per chunk (one row-sum exchange per chunk)
 constexpr int kLagC = 2;                // chunks between a chunk's row sums and its K^T step (3: 2.4 % slower on c1, 1: 17 %)
 constexpr int kNRed = kLagC + 1;        // chunk slots of the warp partials
 constexpr int kRNS = 5;                 // chunk slots of the row-sum channel (> kLagC + 1)
@@ -96,15 +94,20 @@ struct Cfg {
   static constexpr int EPC = 16 / ES;                  // elements per 16-byte chunk
   static constexpr int NE = EPC * NCH;                 // columns per thread
   static constexpr int W = kCons * NE;                 // columns per CTA (slice)
-  static constexpr int R = kStageBytes / (W * ES);     // rows per block
+  static constexpr int SB = kF64 ? 32768 : 65536;      // bytes of a row block of the slice
+  static constexpr int NSA = kF64 ? 3 : 2;             // stages of the ring from HBM (A steps)
+  static constexpr int NSB = kF64 ? 2 : 1;             // stages of the ring from L2 (B steps)
+  static constexpr int NST = NSA + NSB;
+  static constexpr int CB = kF64 ? 4 : 2;              // row blocks per chunk (one row-sum exchange each)
+  static constexpr int R = SB / (W * ES);              // rows per block
   static constexpr int NBOX = W / kBoxW;               // TMA boxes per block
   static constexpr int BOXB = kBoxW * R * ES;          // bytes per box
   static constexpr int RWPR = kF64 ? 4 : 3;            // message words per row
   static constexpr int RW = RWPR * R;                  // row-sum words per block
-  static constexpr int RC = R * kCB;                   // rows per chunk
+  static constexpr int RC = R * CB;                    // rows per chunk
   static constexpr int RCW = RWPR * RC;                // row-sum words per chunk
   static constexpr int RCWP = (RCW + 3) & ~3;          // padded to 16 bytes
-  static_assert(R >= 1 && R * W * ES == kStageBytes, "a stage holds whole rows");
+  static_assert(R >= 1 && R * W * ES == SB, "a stage holds whole rows");
   static_assert(RCWP <= kRCW, "row message too long");
   static_assert(RC <= 32, "a chunk's rows fit a warp");
   static_assert(kBoxW % EPC == 0, "a chunk never straddles two boxes");
@@ -352,14 +355,14 @@ struct FState {
 
 template <int DT, int NCH>
 struct alignas(128) FSmem {
-  uint8_t stage[kNST][kStageBytes];
+  uint8_t stage[Cfg<DT, NCH>::NST][Cfg<DT, NCH>::SB];
   uint32_t red[kNRed][kWarps][kRCW];      // warp partials of a chunk's row sums
   uint32_t rx[kRNS][kCMax][kRCW];         // row-sum messages, one row per sender rank
   uint32_t xout[kRNS][kRCW];              // this CTA's outgoing messages (bulk-copied to the cluster)
   uint32_t sx[kSNS][kCMax][kSWMax];       // scalar messages
   uint32_t wred[kWarps][kBW];             // warp partials of block reductions
   uint32_t bc[2][kBW];                    // block/cluster reduction results (alternating)
-  uint64_t full[kNST], empty[kNST];
+  uint64_t full[Cfg<DT, NCH>::NST], empty[Cfg<DT, NCH>::NST];
   uint64_t redfull[kNRed];
   uint64_t rfull[kRNS], rempty[kRNS];
   uint64_t tfull[kNTot], tcons[kNTot];
@@ -1101,16 +1104,16 @@ struct FC {
     constexpr int AW = kF64 ? 2 : 1;
     const bool fwd = (s & 1) == 0;
     const int nb = bk1 - bk0;
-    const int ncks = (nb + kCB - 1) / kCB;
+    const int ncks = (nb + CF::CB - 1) / CF::CB;
     const bool dots = !(SETUP && a.x0_zero);
     const V* yg = static_cast<const V*>(a.y);
     const uint32_t rs0 = rseq;
 #pragma unroll 1
     for (int c = 0; c < ncks + kLagC; ++c) {
       const bool hasA = c < ncks, hasB = c >= kLagC;
-      const int cntA = hasA ? min(kCB, nb - c * kCB) : 0;
+      const int cntA = hasA ? min(CF::CB, nb - c * CF::CB) : 0;
       const int cb = c - kLagC;
-      const int cntB = hasB ? min(kCB, nb - cb * kCB) : 0;
+      const int cntB = hasB ? min(CF::CB, nb - cb * CF::CB) : 0;
       const uint32_t seq = rs0 + c, s3 = seq % kNRed;
       const uint32_t m = rs0 + cb, ts = m % kNTot;
       bool okt = true;
@@ -1120,13 +1123,13 @@ struct FC {
       bool vch = false;
       if (hasA && dots && warp == 0 && lane < RC) {
         const int jj = lane / R;
-        const int qb = c * kCB + jj;
+        const int qb = c * CF::CB + jj;
         const int row = (fwd ? bk0 + qb : bk1 - 1 - qb) * R + lane % R;
         vch = jj < cntA && row < n;
         if (vch) ych = static_cast<A>(yg[row]);
       }
 #pragma unroll 1
-      for (int j = 0; j < kCB; ++j) {
+      for (int j = 0; j < CF::CB; ++j) {
         // ---- step A: block j of chunk c (from HBM): its row sums
         if (hasA) {
           if (j < cntA) {
@@ -1135,7 +1138,7 @@ struct FC {
             if (dots && ok) row_partials<ACC>(sm.stage[st], &sm.red[s3][warp][RWPR * R * j]);
             __syncwarp();
             if (lane == 0 && ok) mbar_arrive(&sm.empty[st]);
-            if (++sta == kNSA) {
+            if (++sta == CF::NSA) {
               sta = 0;
               pha ^= 1u;
             }
@@ -1146,7 +1149,7 @@ struct FC {
         // ---- step B: block j of chunk c - kLagC (from L2): its K^T step
         if (hasB && j < cntB) {
           if (dots && j == 0) okt = wwait(&sm.tfull[ts], (m / kNTot) & 1u, kSiteRowMsg, false);
-          const int qb = cb * kCB + j;
+          const int qb = cb * CF::CB + j;
           const int b = fwd ? bk0 + qb : bk1 - 1 - qb;
           A m1[R], m2[R];
           if (dots) {
@@ -1174,7 +1177,7 @@ struct FC {
               m2[qq] = A(0);
             }
           }
-          const uint32_t st = kNSA + stb;
+          const uint32_t st = CF::NSA + stb;
           const bool ok = wwait(&sm.full[st], phb, kSitePassB, false);
           if (ok && okt) {
             const uint8_t* stg = sm.stage[st];
@@ -1220,7 +1223,7 @@ struct FC {
           }
           __syncwarp();
           if (lane == 0 && ok) mbar_arrive(&sm.empty[st]);
-          if (++stb == kNSB) {
+          if (++stb == CF::NSB) {
             stb = 0;
             phb ^= 1u;
           }
@@ -1893,7 +1896,7 @@ struct FC {
       // completed their phases before it could be issued)
       for (int ring = 0; ring < 2; ++ring) {
         const uint32_t issued = static_cast<uint32_t>(ctl[ring ? CTL_ISSUED_B : CTL_ISSUED]);
-        const uint32_t ns = ring ? kNSB : kNSA, base = ring ? kNSA : 0;
+        const uint32_t ns = ring ? CF::NSB : CF::NSA, base = ring ? CF::NSA : 0;
         for (uint32_t s = 0; s < ns && s < issued; ++s) {
           const uint32_t last = issued - 1 - ((issued - 1 - s) % ns);
           const uint32_t par = (last / ns) & 1u;
@@ -2372,9 +2375,9 @@ __device__ void producer(const FArgs& a, const CUtensorMap* tmap, FSmem<DT, NCH>
     uint64_t t0 = globaltimer();
     for (unsigned poll = 0;; ++poll) {
       bool did = false;
-      if (mbar_test(&sm.empty[ia % kNSA], ((ia / kNSA) & 1u) ^ 1u)) {
+      if (mbar_test(&sm.empty[ia % CF::NSA], ((ia / CF::NSA) & 1u) ^ 1u)) {
         if (ctl[CTL_STOP]) goto done;
-        load(static_cast<int>(ia % kNSA), block_of(pa, qa));
+        load(static_cast<int>(ia % CF::NSA), block_of(pa, qa));
         ++ia;
         ctl[CTL_ISSUED] = static_cast<int>(ia);
         if (++qa == nb) {
@@ -2383,9 +2386,9 @@ __device__ void producer(const FArgs& a, const CUtensorMap* tmap, FSmem<DT, NCH>
         }
         did = true;
       }
-      if (ib < ia && mbar_test(&sm.empty[kNSA + ib % kNSB], ((ib / kNSB) & 1u) ^ 1u)) {
+      if (ib < ia && mbar_test(&sm.empty[CF::NSA + ib % CF::NSB], ((ib / CF::NSB) & 1u) ^ 1u)) {
         if (ctl[CTL_STOP]) goto done;
-        load(static_cast<int>(kNSA + ib % kNSB), block_of(pb, qb));
+        load(static_cast<int>(CF::NSA + ib % CF::NSB), block_of(pb, qb));
         ++ib;
         ctl[CTL_ISSUED_B] = static_cast<int>(ib);
         if (++qb == nb) {
@@ -2433,7 +2436,7 @@ __global__ void __launch_bounds__(kThr, 1) fused_kernel(const __grid_constant__ 
     return;
   }
   if (tid == 0) {
-    for (int s = 0; s < kNST; ++s) {
+    for (int s = 0; s < Cfg<DT, NCH>::NST; ++s) {
       mbar_init(&sm.full[s], 1);
       mbar_init(&sm.empty[s], kWarps);
     }
